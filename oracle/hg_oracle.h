@@ -1,0 +1,84 @@
+/*
+ * HashGPU CPU oracle -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, obviously correct C99 restatement of what the hashing hot
+ * path computes, used by the test-suite, the smoke check and the CPU baseline
+ * of the benchmark to judge the CUDA library. It shares no code, header,
+ * table or constant generator with the CUDA path, and the product never
+ * links, loads or calls it.
+ *
+ * Every routine cites the passage of "GPUs as Storage System Accelerators"
+ * (Al-Kiswany, Gharaibeh, Ripeanu) or of the hash standard it follows.
+ * Pins (what each routine is checked against in the CPU test-suite):
+ *   hgo_md5 / hgo_sha1        -> hashlib (OpenSSL) at every length 0..2048 and
+ *                                on random MiB-sized inputs
+ *   hgo_hash_blocks           -> hashlib per block and over the digest list
+ *   hgo_window_hash/_candidates -> hashlib.md5 of every window (brute force)
+ *   hgo_select                -> hand-worked fixtures in tests/golden and a
+ *                                checker of the properties that determine the
+ *                                greedy chunking uniquely
+ *   hgo_hash_chunks           -> hashlib per chunk
+ * Nothing here is "parity unpinned".
+ */
+#ifndef HG_ORACLE_H
+#define HG_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { HGO_MD5 = 0, HGO_SHA1 = 1 };
+
+/* RFC 1321: MD5 of len bytes; 16-byte digest in the standard byte order. */
+void hgo_md5(const uint8_t *msg, uint64_t len, uint8_t out[16]);
+/* FIPS 180-4 Sec. 6.1: SHA-1 of len bytes; 20-byte big-endian digest. */
+void hgo_sha1(const uint8_t *msg, uint64_t len, uint8_t out[20]);
+/* Digest length of algo (16 or 20), 0 for an unknown algo. */
+int hgo_digest_len(int algo);
+/* Digest of len bytes with algo; returns 0, or -1 for an unknown algo. */
+int hgo_digest(int algo, const uint8_t *msg, uint64_t len, uint8_t *out);
+
+/*
+ * Direct hashing (Sec. 2.1 "Direct Hashing", Sec. 3.2.2): digest of every
+ * fixed-size block [i*block, min((i+1)*block, n)), then, when root is not
+ * NULL, the hash-of-hashes over the block digests concatenated in block order.
+ * Returns the number of blocks, or -1 on bad arguments.
+ */
+int64_t hgo_hash_blocks(int algo, const uint8_t *in, uint64_t n, uint64_t block,
+                        uint8_t *digests, uint8_t *root);
+
+/*
+ * Sliding-window hash (Sec. 2.1 "Content-based chunking", Sec. 3.2.2): the
+ * first four MD5 digest bytes, read little-endian, of the `window` bytes at win.
+ */
+uint32_t hgo_window_hash(const uint8_t *win, uint32_t window);
+
+/*
+ * Boundary candidates: every cut position c = p + 1, p in [window-1, n-1],
+ * whose window hash h (of bytes p-window+1..p) satisfies
+ * (h & (2^mask_bits - 1)) == magic. Written in increasing order, at most cap
+ * of them; returns the total count. nthreads > 1 splits the positions into
+ * that many contiguous ranges handled by POSIX threads.
+ */
+uint64_t hgo_window_candidates(const uint8_t *in, uint64_t n, uint32_t window,
+                               uint32_t mask_bits, uint32_t magic,
+                               uint64_t *cuts, uint64_t cap, int nthreads);
+
+/*
+ * Chunk boundary selection with minimum and maximum chunk sizes (Sec. 2.1,
+ * Sec. 4.3 workload set-up): chunk ends, strictly increasing, the last one n.
+ * At most cap written; returns the total count.
+ */
+uint64_t hgo_select(const uint64_t *cands, uint64_t ncand, uint64_t n,
+                    uint64_t min_chunk, uint64_t max_chunk,
+                    uint64_t *ends, uint64_t cap);
+
+/* Per-chunk digests (Fig. 3): chunk i is [ends[i-1] (0 for i = 0), ends[i]). */
+int hgo_hash_chunks(int algo, const uint8_t *in, const uint64_t *ends,
+                    uint64_t nchunk, uint8_t *digests);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
