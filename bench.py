@@ -1,0 +1,432 @@
+#!/usr/bin/env python3
+"""Benchmark of the HashGPU hot path on B300.
+
+Workload (one step): content-defined chunking of two versions of a file --
+a 64 MiB seeded uniform base and a second version made by seeded edits
+touching 1 % of its bytes (insert/delete/overwrite runs of 1..512 bytes) --
+with a 20-byte MD5 window at every offset, boundaries where the low 13 bits
+of the window hash equal 0x0F0F, chunks between 2 KiB and 64 KiB, then the
+MD5 digest of every chunk (Sec. 2.1, Sec. 3.2.2, Fig. 3). The two versions
+run on two streams, each with its own library context.
+
+value: hashed GB/s (input bytes of both versions per step / device time per
+step), inputs resident in HBM, L2 flushed between steps.
+e2e:   the same, through the same C-ABI calls, with the versions in pinned
+host memory: H2D of the inputs and D2H of boundaries + digests inside the
+timed region.
+The line also carries the roofline of the dominant kernel (the window-hash
+kernel), the CPU oracle baseline, the fixed-block direct-hashing throughputs
+(1 GiB, MD5/SHA-1, 4 KiB blocks) and the clocks seen while timing.
+
+--impl reference times the CPU oracle on the host cores on bounded samples of
+the same workload (there is no reference implementation to install).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "hashed GB/s (CDC: 20-byte MD5 window + min/max boundaries + per-chunk MD5)"
+UNIT = "GB/s"
+WORKLOAD = "cdc_64MiB_base_plus_1pct_edited_version"
+OPS_PER_WINDOW = 270          # algorithmic 32-bit integer ops per window hash
+INT_LANES_PER_SM_CLK = 128    # 4 schedulers x 32 lanes issue per SM per clock
+WINDOW_KERNEL_SRC = os.path.join(ROOT, "paper_1202_3669_b300", "csrc", "hg_cdc.cu")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="skip direct-hash and CPU legs")
+    return ap.parse_args()
+
+
+def workload():
+    from gen import inputs as G
+    base = G.uniform_bytes(64 << 20, seed=2)
+    v2, _ = G.edited_version(base, seed=3)
+    return [base, v2]
+
+
+# ------------------------------------------------------------------ clocks --------------------
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while timing."""
+    Q = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id: str | None):
+        self.bus = (bus_id or "").lower()
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except FileNotFoundError:
+            self.p = None
+        time.sleep(0.25)
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.p.terminate()
+        self.p.wait()
+        self.f.seek(0)
+        rows = [r.split(", ") for r in self.f.read().strip().splitlines() if r.count(",") >= 9]
+        os.unlink(self.f.name)
+        if self.bus:
+            mine = [r for r in rows if r[1].lower().endswith(self.bus[-12:])]
+            rows = mine or rows
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        idx0 = rows[0][0]
+        rows = [r for r in rows if r[0] == idx0]
+        sm = [float(r[2]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[6 + k].strip() == "Active"})
+        loaded = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": float(rows[0][3]),
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(float(r[4]) for r in rows if r[4].replace('.', '', 1).isdigit()) if rows else None}
+
+
+# ------------------------------------------------------------------ helpers -------------------
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6400.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+def kernel_traffic(kernel: str, src: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on this source."""
+    p = os.path.join(ROOT, "profiles", f"{kernel}.traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        rec = json.load(f)
+    with open(src, "rb") as f:
+        h = hashlib.sha256(f.read()).hexdigest()[:16]
+    if rec.get("source_sha256_16") != h:
+        return None
+    return rec
+
+
+def cpu_baseline(versions, budget_s: float = 12.0):
+    """The oracle as it stands, on the host cores, on a bounded sample of the workload."""
+    import oracle
+    nthreads = os.cpu_count() or 1
+    L = oracle.lib()
+    # calibrate on 256 KiB, then size the sample to about budget_s seconds
+    probe = versions[0][: 256 << 10]
+    t0 = time.perf_counter()
+    e = oracle.cdc(probe, nthreads=nthreads, L=L)
+    oracle.hash_chunks(oracle.MD5, probe, e, L=L)
+    rate = probe.size / max(1e-6, time.perf_counter() - t0)
+    nbytes = int(min(versions[0].size, max(1 << 20, rate * budget_s / 2)))
+    total, t0 = 0, time.perf_counter()
+    for v in versions:
+        s = v[:nbytes]
+        e = oracle.cdc(s, nthreads=nthreads, L=L)
+        oracle.hash_chunks(oracle.MD5, s, e, L=L)
+        total += s.size
+    dt = time.perf_counter() - t0
+    return {"value": total / dt / 1e9, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+            "sample": f"first {nbytes} bytes of each of the two versions ({total} bytes), "
+                      f"window candidates on {nthreads} threads + selection + per-chunk MD5",
+            "seconds": dt}
+
+
+# ------------------------------------------------------------------ reference arm -------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    versions = workload()
+    import oracle
+    nthreads = os.cpu_count() or 1
+    per_step = (2 << 20)          # bytes of each version per step: a bounded sample
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        for v in versions:
+            s = v[:per_step]
+            e = oracle.cdc(s, nthreads=nthreads)
+            oracle.hash_chunks(oracle.MD5, s, e)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+        if sum(times) > 150:      # keep the run within a few minutes
+            break
+    t = sum(times) / len(times)
+    val = 2 * per_step / t / 1e9
+    out = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": len(times),
+           "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+           "impl": "reference",
+           "config": {"workload": WORKLOAD, "sample_bytes_per_version": per_step},
+           "cpu_baseline": {"value": val, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+                            "sample": f"first {per_step} bytes of each version per step"},
+           "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------ our arm -------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    import paper_1202_3669_b300 as hgb
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    versions = workload()
+    nbytes = sum(v.size for v in versions)
+    p = hgb.default_params()
+    ctxs = [hgb.Context(local) for _ in versions]
+    streams = [torch.cuda.Stream(dev) for _ in versions]
+    d_in = [torch.from_numpy(v).to(dev) for v in versions]
+    cap = [v.size // p.min_chunk + 2 for v in versions]
+    ends = [torch.empty(c, dtype=torch.int64, device=dev) for c in cap]
+    cnts = [torch.zeros(1, dtype=torch.int64, device=dev) for _ in versions]
+    dgs = [torch.empty((c, 16), dtype=torch.uint8, device=dev) for c in cap]
+    for c, v in zip(ctxs, versions):
+        c.reserve(v.size)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)    # > 126 MB L2
+    main_s = torch.cuda.current_stream(dev)
+
+    def step(src):
+        ev0 = torch.cuda.Event()
+        ev0.record(main_s)
+        for i in range(len(versions)):
+            s = streams[i]
+            s.wait_event(ev0)
+            ctxs[i].cdc_boundaries(src[i], p, cap=cap[i], out=ends[i], count=cnts[i], stream=s)
+            ctxs[i].hash_chunks(src[i], ends[i], hgb.MD5, count=cnts[i], out=dgs[i], stream=s)
+        for s in streams:
+            main_s.wait_stream(s)
+
+    launches_per_step = 5 * len(versions)    # window, scan, compact, select, chunk hash
+    for _ in range(args.warmup):
+        step(d_in)
+    torch.cuda.synchronize()
+    for c in ctxs:
+        c.sync()
+
+    bus = None
+    try:
+        bus = torch.cuda.get_device_properties(dev).pci_bus_id
+    except Exception:
+        pass
+    clk = ClockSampler(bus)
+    clk.start()
+    barrier()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(main_s)
+        step(d_in)
+        b.record(main_s)
+        ms.append((a, b))
+    torch.cuda.synchronize()
+    barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ms]
+    t_dev = sum(step_ms) / len(step_ms)
+
+    # e2e: pinned host inputs -> device -> boundaries + digests -> pinned host
+    h_in = [torch.from_numpy(v).pin_memory() for v in versions]
+    h_ends = [torch.empty(c, dtype=torch.int64).pin_memory() for c in cap]
+    h_cnt = [torch.empty(1, dtype=torch.int64).pin_memory() for _ in versions]
+    h_dg = [torch.empty((c, 16), dtype=torch.uint8).pin_memory() for c in cap]
+    d_in2 = [torch.empty_like(x) for x in d_in]
+    h2d = sum(v.size for v in versions)
+    d2h = sum(e.numel() * 8 + 8 + d.numel() for e, d in zip(h_ends, h_dg))
+
+    def e2e_step():
+        ev0 = torch.cuda.Event()
+        ev0.record(main_s)
+        for i in range(len(versions)):
+            s = streams[i]
+            s.wait_event(ev0)
+            with torch.cuda.stream(s):
+                d_in2[i].copy_(h_in[i], non_blocking=True)
+            ctxs[i].cdc_boundaries(d_in2[i], p, cap=cap[i], out=ends[i], count=cnts[i], stream=s)
+            ctxs[i].hash_chunks(d_in2[i], ends[i], hgb.MD5, count=cnts[i], out=dgs[i], stream=s)
+            with torch.cuda.stream(s):
+                h_cnt[i].copy_(cnts[i], non_blocking=True)
+                h_ends[i].copy_(ends[i], non_blocking=True)
+                h_dg[i].copy_(dgs[i], non_blocking=True)
+        for s in streams:
+            main_s.wait_stream(s)
+
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_steps = max(10, args.steps // 4)
+    barrier()
+    ev = []
+    for _ in range(e2e_steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(main_s)
+        e2e_step()
+        b.record(main_s)
+        ev.append((a, b))
+    torch.cuda.synchronize()
+    t_e2e = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
+    clocks = clk.stop()
+    for c in ctxs:
+        c.sync()
+
+    # the e2e result must be the device result
+    for i in range(len(versions)):
+        k = int(h_cnt[i].item())
+        assert k == int(cnts[i].item())
+        assert torch.equal(h_ends[i][:k], ends[i][:k].cpu())
+
+    # dominant kernel alone: the window-hash kernel on the base version, same stream discipline
+    wl = []
+    bm = torch.empty((versions[0].size + 31) // 32, dtype=torch.int32, device=dev)
+    for i in range(args.warmup + 20):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(main_s)
+        ctxs[0].window_bitmap(d_in[0], p, out=bm, stream=main_s)
+        b.record(main_s)
+        if i >= args.warmup:
+            wl.append((a, b))
+    torch.cuda.synchronize()
+    t_win = sum(a.elapsed_time(b) for a, b in wl) / len(wl) / 1e3
+    windows = versions[0].size - (p.window - 1)
+    peaks, peak_kind = measured_peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
+    peak_tops = sm_count * INT_LANES_PER_SM_CLK * sm_max * 1e6 / 1e12
+    achieved = windows * OPS_PER_WINDOW / t_win / 1e12
+    tr = kernel_traffic("k_window_bitmap", WINDOW_KERNEL_SRC)
+    roofline = {"bound": "alu", "kernel": "k_window_bitmap<20>", "achieved": achieved,
+                "peak": peak_tops, "unit": "Tops/s (int32)", "frac": achieved / peak_tops,
+                "peak_kind": f"{sm_count} SMs x {INT_LANES_PER_SM_CLK} int32 lanes/clk x "
+                             f"{sm_max:.0f} MHz (max SM clock, {peak_kind})",
+                "ops_per_window": OPS_PER_WINDOW, "windows_per_launch": windows,
+                "launch_ms": t_win * 1e3, "window_GBps": versions[0].size / t_win / 1e9,
+                "traffic": (tr["dram_bytes_per_launch"] * versions[0].size / tr["input_bytes"]) if tr else None}
+    if clocks.get("sm_mhz"):
+        roofline["frac_at_observed_clock"] = achieved / (peak_tops * clocks["sm_mhz"] / sm_max)
+
+    # shared-chunk fraction between the versions (from this run's device results)
+    k0, k1 = int(cnts[0].item()), int(cnts[1].item())
+    s0 = {bytes(r) for r in dgs[0][:k0].cpu().numpy()}
+    e1 = ends[1][:k1].cpu().numpy()
+    sz1 = np.diff(np.concatenate([[0], e1]))
+    shared = sum(int(s) for s, r in zip(sz1, dgs[1][:k1].cpu().numpy()) if bytes(r) in s0) / versions[1].size
+
+    extras = {}
+    if not args.no_extras and rank == 0:
+        extras["direct"] = direct_leg(hgb, ctxs[0], dev, flush)
+        extras["cpu_baseline"] = cpu_baseline(versions)
+
+    # max over ranks
+    t_dev_all, t_e2e_all = t_dev, t_e2e
+    if world > 1:
+        t = torch.tensor([t_dev, t_e2e], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_dev_all, t_e2e_all = float(t[0]), float(t[1])
+    if rank == 0:
+        value = world * nbytes / (t_dev_all / 1e3) / 1e9
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_dev_all,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+               "data": "synthetic",
+               "config": {"workload": WORKLOAD, "bytes_per_step_per_gpu": nbytes,
+                          "version_bytes": [int(v.size) for v in versions],
+                          "window": p.window, "mask_bits": p.mask_bits, "magic": p.magic,
+                          "min_chunk": p.min_chunk, "max_chunk": p.max_chunk, "digest": "md5",
+                          "chunks": [k0, k1], "shared_fraction": shared,
+                          "l2": "flushed between steps (256 MiB memset)",
+                          "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+               "e2e": {"value": world * nbytes / (t_e2e_all / 1e3) / 1e9, "unit": UNIT,
+                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+               "gpu_launches": launches_per_step * args.steps,
+               "roofline": roofline,
+               "cpu_baseline": extras.get("cpu_baseline"),
+               "clocks": clocks,
+               "step_ms_p50": statistics.median(step_ms), "step_ms_max": max(step_ms)}
+        if "direct" in extras:
+            out["direct"] = extras["direct"]
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def direct_leg(hgb, ctx, dev, flush):
+    """Fixed-block MD5 / SHA-1 over 1 GiB of uniform bytes, 4 KiB blocks (digests only, and
+    digests + hash-of-hashes), kernel time with CUDA events, L2 flushed between launches."""
+    import torch
+    from gen import inputs as G
+    data = torch.from_numpy(G.uniform_bytes(1 << 30, seed=4)).to(dev)
+    res = {}
+    peaks, kind = measured_peaks()
+    s = torch.cuda.current_stream(dev)
+    for algo, name in ((hgb.MD5, "md5"), (hgb.SHA1, "sha1")):
+        dl = 16 if algo == hgb.MD5 else 20
+        out = torch.empty(((1 << 30) // 4096, dl), dtype=torch.uint8, device=dev)
+        rt = torch.empty(dl, dtype=torch.uint8, device=dev)
+        for root in (False, True):
+            ts = []
+            for i in range(8):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(s)
+                ctx.hash_blocks(data, 4096, algo, root=root, out=out, root_out=rt)
+                b.record(s)
+                if i >= 3:
+                    ts.append((a, b))
+            torch.cuda.synchronize()
+            t = sum(a.elapsed_time(b) for a, b in ts) / len(ts) / 1e3
+            key = f"{name}_4KiB" + ("_with_root" if root else "")
+            res[key] = {"GBps": (1 << 30) / t / 1e9, "ms": t * 1e3,
+                        "hbm_frac": (1 << 30) / t / 1e9 / peaks["hbm_gbs"]}
+    ctx.sync()
+    res["note"] = f"1 GiB uniform bytes (seed 4), 262144 blocks; HBM peak {peaks['hbm_gbs']} GB/s ({kind})"
+    return res
+
+
+if __name__ == "__main__":
+    main()

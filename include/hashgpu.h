@@ -1,0 +1,164 @@
+/*
+ * hashgpu.h -- C ABI of the B300 HashGPU hashing library (libhashgpu.so).
+ *
+ * The library offloads the two hashing primitives of "GPUs as Storage System
+ * Accelerators" (Al-Kiswany, Gharaibeh, Ripeanu), Sec. 2.1 and Sec. 3.2.2:
+ *   - direct hashing: the digest of every fixed-size block of a buffer, plus
+ *     the hash-of-hashes over the block digests;
+ *   - content-based chunking: a hash of a small window at every byte offset,
+ *     chunk boundaries where the window hash matches a predefined value under
+ *     minimum and maximum chunk sizes, then the digest of every chunk.
+ * As the paper asks of an offloaded primitive (Sec. 3.1, "Minimizing the
+ * integration effort"), the calls keep the shape of a CPU hash call: bytes
+ * in, digests out, plus a library allocator for pinned host buffers
+ * (Sec. 3.2.4 "Fixed-Size Blocks Hashing Integration") and asynchronous job
+ * submission with completion polling (Sec. 3.2.3).
+ *
+ * Conventions for every call:
+ *  - Pointers named d_* are device pointers on the context's device; h_*
+ *    are host pointers. The caller owns all of them. The context owns only
+ *    its internal scratch memory, which counts against its device budget.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream). Calls
+ *    enqueue work on it and return once it is enqueued; results are valid
+ *    after the stream is synchronised. Calls on one context must not be made
+ *    from two host threads at once, and work on two streams of one context
+ *    must not overlap unless each stream has its own context.
+ *  - Every call returns HG_OK (0) or a negative hg_status. Argument errors are
+ *    detected on the host before anything is enqueued. Errors found on the
+ *    device (a bounded wait that ran out, an inconsistent offsets array) are
+ *    recorded in the context's device error word and returned by the next
+ *    hg_sync() on that context.
+ *  - Digests are written in the standard byte order of each algorithm (the
+ *    bytes of hashlib's digest()): 16 bytes for MD5, 20 for SHA-1. Digest
+ *    buffers must be 4-byte aligned.
+ */
+#ifndef HASHGPU_H
+#define HASHGPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HG_OK = 0,
+    HG_EINVAL = -1,       /* bad argument (null pointer, size, alignment, algo) */
+    HG_ENOMEM = -2,       /* device budget or an allocation exhausted */
+    HG_ECAPACITY = -3,    /* an output array was too small (count still reported) */
+    HG_ETIMEDOUT = -4,    /* a bounded device-side wait gave up */
+    HG_ECUDA = -5,        /* a CUDA runtime call failed */
+    HG_EAGAIN = -6,       /* asynchronous result not ready yet */
+    HG_ECANCELED = -7,    /* request cancelled before it ran */
+    HG_EUNSUPPORTED = -8  /* parameters outside what this build supports */
+} hg_status;
+
+typedef enum { HG_MD5 = 0, HG_SHA1 = 1 } hg_algo;
+
+typedef struct hg_ctx hg_ctx;
+
+/*
+ * Content-defined chunking parameters (Sec. 2.1 "Content-based chunking";
+ * min/max chunk sizes as in the Sec. 4.3 set-up). A window of `window` bytes
+ * ends at every offset p >= window-1; its hash h is the first four MD5 digest
+ * bytes read little-endian; when (h & (2^mask_bits - 1)) == magic the
+ * position p + 1 is a candidate cut. Cuts are chosen greedily from offset 0:
+ * from chunk start s, the first candidate c with s + min_chunk <= c <=
+ * s + max_chunk; with none, s + max_chunk if that is < n, else n.
+ * Supported: 1 <= window <= 55, 1 <= mask_bits <= 32, magic < 2^mask_bits,
+ * 1 <= min_chunk <= max_chunk.
+ */
+typedef struct {
+    uint32_t window;     /* bytes per window (20) */
+    uint32_t mask_bits;  /* low bits of the window hash compared (13) */
+    uint32_t magic;      /* value they must equal (0x0F0F) */
+    uint32_t reserved;   /* must be 0 */
+    uint64_t min_chunk;  /* 2048 */
+    uint64_t max_chunk;  /* 65536 */
+} hg_cdc_params;
+
+/* Fill p with the defaults used throughout (20, 13, 0x0F0F, 2 KiB, 64 KiB). */
+void hg_cdc_default_params(hg_cdc_params *p);
+
+/* Human-readable name of a status code (static string). */
+const char *hg_strerror(int status);
+
+/* Digest length in bytes of algo (16, 20), or HG_EINVAL. */
+int hg_digest_len(int algo);
+
+/*
+ * Create a context on CUDA device `device`. `device_budget_bytes` caps the
+ * scratch memory the context may hold (0 = 32 GiB). Scratch is allocated on
+ * first use and grown as needed; hg_reserve() allocates it ahead of time.
+ */
+int hg_init(hg_ctx **out, int device, size_t device_budget_bytes);
+/* Free the context and all its scratch (synchronises its device first). */
+int hg_destroy(hg_ctx *ctx);
+/* Pre-allocate scratch for chunking inputs of up to max_bytes bytes. */
+int hg_reserve(hg_ctx *ctx, uint64_t max_bytes);
+/* Synchronise `stream` and return (then clear) the device error word. */
+int hg_sync(hg_ctx *ctx, void *stream);
+/* Bytes of scratch currently held by the context. */
+uint64_t hg_scratch_bytes(const hg_ctx *ctx);
+
+/*
+ * Direct hashing, Sec. 2.1 "Direct Hashing" and Sec. 3.2.2: the digest of
+ * every block [i*block, min((i+1)*block, n)) of d_in (the last block may be
+ * short), written to d_digests[i*dlen .. (i+1)*dlen), nblk = ceil(n/block).
+ * If d_root is not NULL it receives the hash-of-hashes: the digest, with the
+ * same algorithm, of the nblk*dlen digest bytes in block order (Sec. 3.2.2,
+ * the final step that hashes the buffer of intermediate digests). n = 0 gives
+ * no blocks and the digest of the empty string as root.
+ * d_in: n bytes, any alignment. d_digests: nblk*dlen bytes, 4-byte aligned.
+ * d_root: dlen bytes or NULL. Errors: HG_EINVAL (block == 0, bad algo,
+ * null or misaligned buffer).
+ */
+int hg_hash_blocks(hg_ctx *ctx, int algo, const uint8_t *d_in, uint64_t n, uint64_t block,
+                   uint8_t *d_digests, uint8_t *d_root, void *stream);
+
+/*
+ * Sliding-window hashing, Sec. 3.2.2 "Content-based chunking": bit p of the
+ * bitmap (word p/32, bit p%32) is set when the window ending at byte p is a
+ * candidate (see hg_cdc_params); bits for p < window-1 and p >= n are 0.
+ * d_bitmap: ceil(n/32) uint32 words.
+ */
+int hg_window_bitmap(hg_ctx *ctx, const uint8_t *d_in, uint64_t n, const hg_cdc_params *params,
+                     uint32_t *d_bitmap, void *stream);
+
+/*
+ * Candidate cut positions (the window-hash test of Sec. 2.1 followed by the
+ * boundary check the paper leaves to the CPU in Sec. 3.2.2, done here on the
+ * device): all c = p + 1 with window p a candidate, increasing. At most cap
+ * are written to d_cands; the total count goes to *d_count (device uint64).
+ */
+int hg_cdc_candidates(hg_ctx *ctx, const uint8_t *d_in, uint64_t n, const hg_cdc_params *params,
+                      uint64_t *d_cands, uint64_t cap, uint64_t *d_count, void *stream);
+
+/*
+ * Chunk boundaries, Sec. 2.1 with the min/max rule of hg_cdc_params: chunk
+ * end offsets, strictly increasing, the last equal to n (none when n = 0).
+ * At most cap are written to d_ends; the total count goes to *d_count
+ * (device uint64). A count above cap means d_ends was too small. With cap >=
+ * n/min_chunk + 1 it never is.
+ */
+int hg_cdc_boundaries(hg_ctx *ctx, const uint8_t *d_in, uint64_t n, const hg_cdc_params *params,
+                      uint64_t *d_ends, uint64_t cap, uint64_t *d_count, void *stream);
+
+/*
+ * Per-chunk digests, Fig. 3 (the second job, direct hashing of each chunk):
+ * chunk i is [d_ends[i-1] (0 for i = 0), d_ends[i]) of the n-byte input d_in.
+ * nchunk is the host-side number of entries; when d_count is not NULL the
+ * number actually hashed is min(nchunk, *d_count) (as written by
+ * hg_cdc_boundaries), so the two calls chain on one stream without a host
+ * round trip. d_digests: nchunk*dlen bytes, 4-byte aligned. An end that is
+ * below the previous one or above n records HG_EINVAL in the device error
+ * word and leaves that digest unwritten.
+ */
+int hg_hash_chunks(hg_ctx *ctx, int algo, const uint8_t *d_in, uint64_t n, const uint64_t *d_ends,
+                   uint64_t nchunk, const uint64_t *d_count, uint8_t *d_digests, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HASHGPU_H */

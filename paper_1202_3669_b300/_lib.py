@@ -1,0 +1,124 @@
+"""ctypes binding of libhashgpu.so (include/hashgpu.h).
+
+The raw functions keep the C names and argument order (pointers are passed
+as integers). Nothing here computes anything: every step runs in the CUDA
+library, and importing this module fails loudly when the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libhashgpu.so")
+
+HG_OK, HG_EINVAL, HG_ENOMEM, HG_ECAPACITY, HG_ETIMEDOUT = 0, -1, -2, -3, -4
+HG_ECUDA, HG_EAGAIN, HG_ECANCELED, HG_EUNSUPPORTED = -5, -6, -7, -8
+HG_MD5, HG_SHA1 = 0, 1
+
+# every exported symbol the header declares, with (restype, argtypes)
+_vp, _u64, _u32, _i32, _sz = C.c_void_p, C.c_uint64, C.c_uint32, C.c_int, C.c_size_t
+
+
+class hg_cdc_params(C.Structure):
+    _fields_ = [("window", C.c_uint32), ("mask_bits", C.c_uint32), ("magic", C.c_uint32),
+                ("reserved", C.c_uint32), ("min_chunk", C.c_uint64), ("max_chunk", C.c_uint64)]
+
+
+SIGNATURES = {
+    "hg_cdc_default_params": (None, [C.POINTER(hg_cdc_params)]),
+    "hg_strerror": (C.c_char_p, [_i32]),
+    "hg_digest_len": (_i32, [_i32]),
+    "hg_init": (_i32, [C.POINTER(_vp), _i32, _sz]),
+    "hg_destroy": (_i32, [_vp]),
+    "hg_reserve": (_i32, [_vp, _u64]),
+    "hg_sync": (_i32, [_vp, _vp]),
+    "hg_scratch_bytes": (_u64, [_vp]),
+    "hg_hash_blocks": (_i32, [_vp, _i32, _vp, _u64, _u64, _vp, _vp, _vp]),
+    "hg_window_bitmap": (_i32, [_vp, _vp, _u64, C.POINTER(hg_cdc_params), _vp, _vp]),
+    "hg_cdc_candidates": (_i32, [_vp, _vp, _u64, C.POINTER(hg_cdc_params), _vp, _u64, _vp, _vp]),
+    "hg_cdc_boundaries": (_i32, [_vp, _vp, _u64, C.POINTER(hg_cdc_params), _vp, _u64, _vp, _vp]),
+    "hg_hash_chunks": (_i32, [_vp, _i32, _vp, _u64, _vp, _u64, _vp, _vp, _vp]),
+}
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(
+            f"{path} is missing: build the CUDA library first "
+            "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = load()
+
+
+class HashGPUError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        msg = lib.hg_strerror(status).decode()
+        super().__init__(f"{what}: {msg} ({status})" if what else f"{msg} ({status})")
+
+
+def check(status: int, what: str = "") -> int:
+    if status != HG_OK:
+        raise HashGPUError(status, what)
+    return status
+
+
+def default_params() -> hg_cdc_params:
+    p = hg_cdc_params()
+    lib.hg_cdc_default_params(C.byref(p))
+    return p
+
+
+# ---- raw C names, same argument order -------------------------------------------------------
+def hg_init(device: int = 0, budget: int = 0) -> int:
+    h = _vp()
+    check(lib.hg_init(C.byref(h), device, budget), "hg_init")
+    return h.value
+
+
+def hg_destroy(ctx: int) -> int:
+    return lib.hg_destroy(ctx)
+
+
+def hg_reserve(ctx: int, max_bytes: int) -> int:
+    return lib.hg_reserve(ctx, max_bytes)
+
+
+def hg_sync(ctx: int, stream: int | None) -> int:
+    return lib.hg_sync(ctx, stream)
+
+
+def hg_scratch_bytes(ctx: int) -> int:
+    return lib.hg_scratch_bytes(ctx)
+
+
+def hg_digest_len(algo: int) -> int:
+    return lib.hg_digest_len(algo)
+
+
+def hg_hash_blocks(ctx, algo, d_in, n, block, d_digests, d_root, stream) -> int:
+    return lib.hg_hash_blocks(ctx, algo, d_in, n, block, d_digests, d_root, stream)
+
+
+def hg_window_bitmap(ctx, d_in, n, params, d_bitmap, stream) -> int:
+    return lib.hg_window_bitmap(ctx, d_in, n, C.byref(params), d_bitmap, stream)
+
+
+def hg_cdc_candidates(ctx, d_in, n, params, d_cands, cap, d_count, stream) -> int:
+    return lib.hg_cdc_candidates(ctx, d_in, n, C.byref(params), d_cands, cap, d_count, stream)
+
+
+def hg_cdc_boundaries(ctx, d_in, n, params, d_ends, cap, d_count, stream) -> int:
+    return lib.hg_cdc_boundaries(ctx, d_in, n, C.byref(params), d_ends, cap, d_count, stream)
+
+
+def hg_hash_chunks(ctx, algo, d_in, n, d_ends, nchunk, d_count, d_digests, stream) -> int:
+    return lib.hg_hash_chunks(ctx, algo, d_in, n, d_ends, nchunk, d_count, d_digests, stream)

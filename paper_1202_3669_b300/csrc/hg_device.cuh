@@ -1,0 +1,251 @@
+// Device-side building blocks of the HashGPU kernels (sm_103a).
+//
+// MD5 (RFC 1321) and SHA-1 (FIPS 180-4) compression functions written as
+// straight-line integer code: every round constant is an instruction
+// immediate, rotations are funnel shifts, and the boolean round functions are
+// left to the compiler as single three-input logic ops. Message words arrive
+// as little-endian 32-bit words (the natural load order); SHA-1 byte-swaps
+// them itself.
+#pragma once
+#include <cstdint>
+
+namespace hg {
+
+__device__ __forceinline__ uint32_t rotl(uint32_t x, int s) { return __funnelshift_l(x, x, s); }
+__device__ __forceinline__ uint32_t bswap(uint32_t x) { return __byte_perm(x, 0, 0x0123); }
+
+// ---------------------------------------------------------------- MD5 ------
+// Round functions of RFC 1321 Sec. 3.4 in select form.
+#define HG_MD5_F(x, y, z) ((z) ^ ((x) & ((y) ^ (z))))
+#define HG_MD5_G(x, y, z) ((y) ^ ((z) & ((x) ^ (y))))
+#define HG_MD5_H(x, y, z) ((x) ^ (y) ^ (z))
+#define HG_MD5_I(x, y, z) ((y) ^ ((x) | ~(z)))
+#define HG_MD5_STEP(f, a, b, c, d, m, k, s)          \
+    do {                                              \
+        (a) += f((b), (c), (d)) + (m) + (uint32_t)(k); \
+        (a) = rotl((a), (s)) + (b);                   \
+    } while (0)
+
+// RFC 1321 Sec. 3.3 initial buffer words A, B, C, D.
+constexpr uint32_t kMd5A = 0x67452301u, kMd5B = 0xefcdab89u, kMd5C = 0x98badcfeu,
+                   kMd5D = 0x10325476u;
+
+// The 64 operations on one block. With FULL = false it stops after operation
+// 61 (index 60), the last one that writes word a, which is all the window
+// test needs; the caller then adds the initial a itself.
+template <bool FULL>
+__device__ __forceinline__ void md5_rounds(uint32_t &a, uint32_t &b, uint32_t &c, uint32_t &d,
+                                           const uint32_t (&M)[16]) {
+    HG_MD5_STEP(HG_MD5_F, a, b, c, d, M[0], 0xd76aa478, 7);
+    HG_MD5_STEP(HG_MD5_F, d, a, b, c, M[1], 0xe8c7b756, 12);
+    HG_MD5_STEP(HG_MD5_F, c, d, a, b, M[2], 0x242070db, 17);
+    HG_MD5_STEP(HG_MD5_F, b, c, d, a, M[3], 0xc1bdceee, 22);
+    HG_MD5_STEP(HG_MD5_F, a, b, c, d, M[4], 0xf57c0faf, 7);
+    HG_MD5_STEP(HG_MD5_F, d, a, b, c, M[5], 0x4787c62a, 12);
+    HG_MD5_STEP(HG_MD5_F, c, d, a, b, M[6], 0xa8304613, 17);
+    HG_MD5_STEP(HG_MD5_F, b, c, d, a, M[7], 0xfd469501, 22);
+    HG_MD5_STEP(HG_MD5_F, a, b, c, d, M[8], 0x698098d8, 7);
+    HG_MD5_STEP(HG_MD5_F, d, a, b, c, M[9], 0x8b44f7af, 12);
+    HG_MD5_STEP(HG_MD5_F, c, d, a, b, M[10], 0xffff5bb1, 17);
+    HG_MD5_STEP(HG_MD5_F, b, c, d, a, M[11], 0x895cd7be, 22);
+    HG_MD5_STEP(HG_MD5_F, a, b, c, d, M[12], 0x6b901122, 7);
+    HG_MD5_STEP(HG_MD5_F, d, a, b, c, M[13], 0xfd987193, 12);
+    HG_MD5_STEP(HG_MD5_F, c, d, a, b, M[14], 0xa679438e, 17);
+    HG_MD5_STEP(HG_MD5_F, b, c, d, a, M[15], 0x49b40821, 22);
+
+    HG_MD5_STEP(HG_MD5_G, a, b, c, d, M[1], 0xf61e2562, 5);
+    HG_MD5_STEP(HG_MD5_G, d, a, b, c, M[6], 0xc040b340, 9);
+    HG_MD5_STEP(HG_MD5_G, c, d, a, b, M[11], 0x265e5a51, 14);
+    HG_MD5_STEP(HG_MD5_G, b, c, d, a, M[0], 0xe9b6c7aa, 20);
+    HG_MD5_STEP(HG_MD5_G, a, b, c, d, M[5], 0xd62f105d, 5);
+    HG_MD5_STEP(HG_MD5_G, d, a, b, c, M[10], 0x02441453, 9);
+    HG_MD5_STEP(HG_MD5_G, c, d, a, b, M[15], 0xd8a1e681, 14);
+    HG_MD5_STEP(HG_MD5_G, b, c, d, a, M[4], 0xe7d3fbc8, 20);
+    HG_MD5_STEP(HG_MD5_G, a, b, c, d, M[9], 0x21e1cde6, 5);
+    HG_MD5_STEP(HG_MD5_G, d, a, b, c, M[14], 0xc33707d6, 9);
+    HG_MD5_STEP(HG_MD5_G, c, d, a, b, M[3], 0xf4d50d87, 14);
+    HG_MD5_STEP(HG_MD5_G, b, c, d, a, M[8], 0x455a14ed, 20);
+    HG_MD5_STEP(HG_MD5_G, a, b, c, d, M[13], 0xa9e3e905, 5);
+    HG_MD5_STEP(HG_MD5_G, d, a, b, c, M[2], 0xfcefa3f8, 9);
+    HG_MD5_STEP(HG_MD5_G, c, d, a, b, M[7], 0x676f02d9, 14);
+    HG_MD5_STEP(HG_MD5_G, b, c, d, a, M[12], 0x8d2a4c8a, 20);
+
+    HG_MD5_STEP(HG_MD5_H, a, b, c, d, M[5], 0xfffa3942, 4);
+    HG_MD5_STEP(HG_MD5_H, d, a, b, c, M[8], 0x8771f681, 11);
+    HG_MD5_STEP(HG_MD5_H, c, d, a, b, M[11], 0x6d9d6122, 16);
+    HG_MD5_STEP(HG_MD5_H, b, c, d, a, M[14], 0xfde5380c, 23);
+    HG_MD5_STEP(HG_MD5_H, a, b, c, d, M[1], 0xa4beea44, 4);
+    HG_MD5_STEP(HG_MD5_H, d, a, b, c, M[4], 0x4bdecfa9, 11);
+    HG_MD5_STEP(HG_MD5_H, c, d, a, b, M[7], 0xf6bb4b60, 16);
+    HG_MD5_STEP(HG_MD5_H, b, c, d, a, M[10], 0xbebfbc70, 23);
+    HG_MD5_STEP(HG_MD5_H, a, b, c, d, M[13], 0x289b7ec6, 4);
+    HG_MD5_STEP(HG_MD5_H, d, a, b, c, M[0], 0xeaa127fa, 11);
+    HG_MD5_STEP(HG_MD5_H, c, d, a, b, M[3], 0xd4ef3085, 16);
+    HG_MD5_STEP(HG_MD5_H, b, c, d, a, M[6], 0x04881d05, 23);
+    HG_MD5_STEP(HG_MD5_H, a, b, c, d, M[9], 0xd9d4d039, 4);
+    HG_MD5_STEP(HG_MD5_H, d, a, b, c, M[12], 0xe6db99e5, 11);
+    HG_MD5_STEP(HG_MD5_H, c, d, a, b, M[15], 0x1fa27cf8, 16);
+    HG_MD5_STEP(HG_MD5_H, b, c, d, a, M[2], 0xc4ac5665, 23);
+
+    HG_MD5_STEP(HG_MD5_I, a, b, c, d, M[0], 0xf4292244, 6);
+    HG_MD5_STEP(HG_MD5_I, d, a, b, c, M[7], 0x432aff97, 10);
+    HG_MD5_STEP(HG_MD5_I, c, d, a, b, M[14], 0xab9423a7, 15);
+    HG_MD5_STEP(HG_MD5_I, b, c, d, a, M[5], 0xfc93a039, 21);
+    HG_MD5_STEP(HG_MD5_I, a, b, c, d, M[12], 0x655b59c3, 6);
+    HG_MD5_STEP(HG_MD5_I, d, a, b, c, M[3], 0x8f0ccc92, 10);
+    HG_MD5_STEP(HG_MD5_I, c, d, a, b, M[10], 0xffeff47d, 15);
+    HG_MD5_STEP(HG_MD5_I, b, c, d, a, M[1], 0x85845dd1, 21);
+    HG_MD5_STEP(HG_MD5_I, a, b, c, d, M[8], 0x6fa87e4f, 6);
+    HG_MD5_STEP(HG_MD5_I, d, a, b, c, M[15], 0xfe2ce6e0, 10);
+    HG_MD5_STEP(HG_MD5_I, c, d, a, b, M[6], 0xa3014314, 15);
+    HG_MD5_STEP(HG_MD5_I, b, c, d, a, M[13], 0x4e0811a1, 21);
+    HG_MD5_STEP(HG_MD5_I, a, b, c, d, M[4], 0xf7537e82, 6);
+    if (FULL) {
+        HG_MD5_STEP(HG_MD5_I, d, a, b, c, M[11], 0xbd3af235, 10);
+        HG_MD5_STEP(HG_MD5_I, c, d, a, b, M[2], 0x2ad7d2bb, 15);
+        HG_MD5_STEP(HG_MD5_I, b, c, d, a, M[9], 0xeb86d391, 21);
+    }
+}
+
+struct Md5 {
+    static constexpr int kDigest = 16;
+    static constexpr int kWords = 4;
+    uint32_t h[4];
+    __device__ __forceinline__ void init() {
+        h[0] = kMd5A; h[1] = kMd5B; h[2] = kMd5C; h[3] = kMd5D;
+    }
+    // M: little-endian message words.
+    __device__ __forceinline__ void compress(const uint32_t (&M)[16]) {
+        uint32_t a = h[0], b = h[1], c = h[2], d = h[3];
+        md5_rounds<true>(a, b, c, d, M);
+        h[0] += a; h[1] += b; h[2] += c; h[3] += d;
+    }
+    // Bit length goes little-endian into words 14, 15.
+    __device__ __forceinline__ static void put_length(uint32_t (&M)[16], uint64_t bytes) {
+        const uint64_t bits = bytes * 8u;
+        M[14] = (uint32_t)bits; M[15] = (uint32_t)(bits >> 32);
+    }
+    // Digest words in output byte order (little-endian words).
+    __device__ __forceinline__ uint32_t out_word(int i) const { return h[i]; }
+};
+
+// --------------------------------------------------------------- SHA-1 -----
+
+struct Sha1 {
+    static constexpr int kDigest = 20;
+    static constexpr int kWords = 5;
+    uint32_t h[5];
+    __device__ __forceinline__ void init() {
+        // FIPS 180-4 Sec. 5.3.1 initial hash value
+        h[0] = 0x67452301u; h[1] = 0xefcdab89u; h[2] = 0x98badcfeu; h[3] = 0x10325476u;
+        h[4] = 0xc3d2e1f0u;
+    }
+    // M: little-endian message words (byte-swapped here to the big-endian
+    // words FIPS 180-4 Sec. 5.2.1 parses).
+    __device__ __forceinline__ void compress(const uint32_t (&M)[16]) {
+        uint32_t W[16];
+#pragma unroll
+        for (int i = 0; i < 16; i++) W[i] = bswap(M[i]);
+        compress_be(W);
+    }
+    __device__ __forceinline__ void compress_be(uint32_t (&W)[16]) {
+        uint32_t a = h[0], b = h[1], c = h[2], d = h[3], e = h[4];
+#pragma unroll
+        for (int t = 0; t < 80; t++) {
+            if (t >= 16)
+                W[t & 15] = rotl(W[(t - 3) & 15] ^ W[(t - 8) & 15] ^ W[(t - 14) & 15] ^ W[t & 15], 1);
+            uint32_t f, k;
+            if (t < 20)      { f = d ^ (b & (c ^ d));       k = 0x5a827999u; }
+            else if (t < 40) { f = b ^ c ^ d;               k = 0x6ed9eba1u; }
+            else if (t < 60) { f = (b & c) | (d & (b | c)); k = 0x8f1bbcdcu; }
+            else             { f = b ^ c ^ d;               k = 0xca62c1d6u; }
+            const uint32_t T = rotl(a, 5) + f + e + k + W[t & 15];
+            e = d; d = c; c = rotl(b, 30); b = a; a = T;
+        }
+        h[0] += a; h[1] += b; h[2] += c; h[3] += d; h[4] += e;
+    }
+    // Bit length goes big-endian into the last two big-endian words, i.e.
+    // byte-swapped into the little-endian message words 14, 15.
+    __device__ __forceinline__ static void put_length(uint32_t (&M)[16], uint64_t bytes) {
+        const uint64_t bits = bytes * 8u;
+        M[14] = bswap((uint32_t)(bits >> 32)); M[15] = bswap((uint32_t)bits);
+    }
+    __device__ __forceinline__ uint32_t out_word(int i) const { return bswap(h[i]); }
+};
+
+// Digest of the len bytes at msg, which may start at any byte address. Full
+// 64-byte blocks are read as aligned 16-byte vectors (the one vector that
+// straddles the end of the message stays inside its aligned 16-byte granule,
+// so it never crosses a page) and shifted into place; the final partial block
+// and the padding are assembled from byte loads inside the message.
+template <class H>
+__device__ void hash_range(const uint8_t *__restrict__ msg, uint64_t len, H &hs) {
+    hs.init();
+    const uint64_t nfull = len >> 6;
+    const uintptr_t addr = reinterpret_cast<uintptr_t>(msg);
+    const uint32_t sh = (uint32_t)(addr & 15);
+    const uint32_t q = sh >> 2, r8 = (sh & 3) * 8;
+    const uint4 *p = reinterpret_cast<const uint4 *>(addr - sh);
+    for (uint64_t k = 0; k < nfull; k++) {
+        uint32_t v[20];
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const uint4 x = __ldg(p + 4 * k + i);
+            v[4 * i] = x.x; v[4 * i + 1] = x.y; v[4 * i + 2] = x.z; v[4 * i + 3] = x.w;
+        }
+        if (sh) {
+            const uint4 x = __ldg(p + 4 * k + 4);
+            v[16] = x.x; v[17] = x.y; v[18] = x.z; v[19] = x.w;
+        } else {
+            v[16] = v[17] = v[18] = v[19] = 0;
+        }
+        // shift by q words, then by r8 bits
+        uint32_t u[17];
+#pragma unroll
+        for (int i = 0; i < 17; i++) {
+            const uint32_t s1 = (q & 1) ? v[i + 1] : v[i];
+            const uint32_t s2 = (q & 1) ? v[i + 3] : v[i + 2];
+            u[i] = (q & 2) ? s2 : s1;
+        }
+        uint32_t M[16];
+#pragma unroll
+        for (int i = 0; i < 16; i++) M[i] = r8 ? __funnelshift_r(u[i], u[i + 1], r8) : u[i];
+        hs.compress(M);
+    }
+    // tail: rem bytes, the 0x80 marker, zeros, the length
+    const uint32_t rem = (uint32_t)(len & 63);
+    const uint8_t *t = msg + (nfull << 6);
+    uint32_t M[16];
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+        uint32_t w = 0;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const uint32_t idx = 4 * i + j;
+            uint32_t byte = idx < rem ? (uint32_t)t[idx] : (idx == rem ? 0x80u : 0u);
+            w |= byte << (8 * j);
+        }
+        M[i] = w;
+    }
+    if (rem < 56) {
+        H::put_length(M, len);
+        hs.compress(M);
+    } else {
+        hs.compress(M);
+        uint32_t Z[16];
+#pragma unroll
+        for (int i = 0; i < 16; i++) Z[i] = 0;
+        H::put_length(Z, len);
+        hs.compress(Z);
+    }
+}
+
+template <class H>
+__device__ __forceinline__ void store_digest(const H &hs, uint8_t *out) {
+    // digests are written word by word; `out` is 4-byte aligned for both algos
+    uint32_t *o = reinterpret_cast<uint32_t *>(out);
+#pragma unroll
+    for (int i = 0; i < H::kWords; i++) o[i] = hs.out_word(i);
+}
+
+}  // namespace hg

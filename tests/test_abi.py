@@ -1,0 +1,61 @@
+"""The C-ABI library loads on the CPU host and exports everything include/*.h declares.
+
+No compute is called here (there is no GPU on the build host); only calls that
+touch no device memory.
+"""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+INCLUDE = os.path.join(ROOT, "include")
+
+
+def declared_functions():
+    names = set()
+    for f in os.listdir(INCLUDE):
+        if not f.endswith(".h"):
+            continue
+        src = open(os.path.join(INCLUDE, f)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"\b(hg_\w+)\s*\(", src))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("hg_hash_blocks", "hg_cdc_boundaries", "hg_hash_chunks", "hg_init", "hg_destroy"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_1202_3669_b300 import _lib
+    lib = C.CDLL(_lib.LIB_PATH)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_symbol():
+    from paper_1202_3669_b300 import _lib
+    assert set(declared_functions()) <= set(_lib.SIGNATURES)
+
+
+def test_host_only_calls():
+    from paper_1202_3669_b300 import _lib
+    L = _lib.lib
+    assert L.hg_digest_len(0) == 16 and L.hg_digest_len(1) == 20 and L.hg_digest_len(7) == -1
+    assert L.hg_strerror(-3) == b"output capacity too small"
+    p = _lib.default_params()
+    assert (p.window, p.mask_bits, p.magic, p.min_chunk, p.max_chunk) == (20, 13, 0x0F0F, 2048, 65536)
+
+
+def test_init_without_gpu_fails_cleanly():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    from paper_1202_3669_b300 import _lib
+    h = C.c_void_p()
+    assert _lib.lib.hg_init(C.byref(h), 0, 0) == _lib.HG_ECUDA
+    assert h.value is None

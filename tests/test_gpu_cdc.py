@@ -1,0 +1,154 @@
+"""GPU parity of content-based chunking (Sec. 2.1, Sec. 3.2.2, Fig. 3) against the oracle.
+
+Window candidates, compaction and boundary offsets are integer results and
+must match exactly; chunk digests byte for byte.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from gen import inputs as G
+from tests.gpu_util import bitmap_to_cuts, to_device
+from tests.pins import check_chunking
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hg():
+    import paper_1202_3669_b300 as hgb
+    ctx = hgb.Context(0)
+    yield ctx
+    ctx.close()
+
+
+def P(**kw):
+    import paper_1202_3669_b300 as hgb
+    return hgb.params(**kw)
+
+
+SIZES = [0, 1, 19, 20, 21, 100, 8191, 8192, 8193, 8192 * 3 + 77, 100_000, (1 << 20) + 13]
+WINDOWS = [(20, 6, 0x2A), (16, 5, 0x11), (17, 5, 0x3), (1, 3, 0x5), (55, 6, 0x3F), (48, 5, 0),
+           (32, 4, 0xA), (24, 5, 0x1F), (33, 6, 0x20), (20, 13, 0x0F0F)]
+
+
+@pytest.mark.parametrize("n", SIZES)
+@pytest.mark.parametrize("window,mask_bits,magic", WINDOWS)
+def test_window_bitmap(hg, n, window, mask_bits, magic):
+    data = G.uniform_bytes(n, seed=n * 7 + window)
+    for off in (0, 3):
+        bm = hg.window_bitmap(to_device(data, off), P(window=window, mask_bits=mask_bits, magic=magic))
+        got = bitmap_to_cuts(bm, n)
+        want = oracle.window_candidates(data, window, mask_bits, magic, nthreads=8)
+        assert np.array_equal(got, want), (off, got[:10], want[:10])
+    hg.sync()
+
+
+@pytest.mark.parametrize("n", [0, 50, 8192 * 5 + 3, 300_000, (2 << 20) + 1])
+@pytest.mark.parametrize("mask_bits", [3, 8, 13])
+def test_candidates(hg, n, mask_bits):
+    data = G.uniform_bytes(n, seed=n + mask_bits)
+    cands, cnt = hg.cdc_candidates(to_device(data), P(mask_bits=mask_bits, magic=1), cap=n + 8)
+    c = int(cnt.item())
+    want = oracle.window_candidates(data, 20, mask_bits, 1, nthreads=8)
+    assert c == want.size
+    assert np.array_equal(cands[:c].cpu().numpy().astype(np.uint64), want)
+    hg.sync()
+
+
+def test_candidates_capacity(hg):
+    data = G.uniform_bytes(200_000, seed=3)
+    want = oracle.window_candidates(data, 20, 6, 1, nthreads=8)
+    cands, cnt = hg.cdc_candidates(to_device(data), P(mask_bits=6, magic=1), cap=10)
+    assert int(cnt.item()) == want.size > 10
+    assert np.array_equal(cands[:10].cpu().numpy().astype(np.uint64), want[:10])
+    hg.sync()
+
+
+def run_cdc(hg, data, algo=oracle.MD5, offset=0, **kw):
+    p = P(**kw)
+    d = to_device(data, offset)
+    ends, cnt, dg = hg.cdc(d, algo, p)
+    c = int(cnt.item())
+    hg.sync()
+    return ends[:c].cpu().numpy().astype(np.uint64), dg[:c].cpu().numpy()
+
+
+@pytest.mark.parametrize("n", [0, 1, 2047, 2048, 2049, 65536, 65537, 200_000, (1 << 20) + 5])
+@pytest.mark.parametrize("kw", [dict(), dict(mask_bits=9, magic=0x55, min_chunk=700, max_chunk=5000),
+                                dict(window=16, mask_bits=8, magic=3, min_chunk=1, max_chunk=300)])
+@pytest.mark.parametrize("offset", [0, 5])
+def test_cdc_small(hg, n, kw, offset):
+    data = G.uniform_bytes(n, seed=n + 99)
+    q = dict(window=20, mask_bits=13, magic=0x0F0F, min_chunk=2048, max_chunk=65536)
+    q.update(kw)
+    ends, dg = run_cdc(hg, data, offset=offset, **q)
+    cands = oracle.window_candidates(data, q["window"], q["mask_bits"], q["magic"], nthreads=8)
+    want = oracle.select(cands, n, q["min_chunk"], q["max_chunk"])
+    assert np.array_equal(ends, want)
+    check_chunking(want.tolist(), cands.tolist(), n, q["min_chunk"], q["max_chunk"])
+    assert np.array_equal(dg, oracle.hash_chunks(oracle.MD5, data, want))
+
+
+def test_cdc_dense_candidates_use_bitmap_path(hg):
+    """More candidates than the list holds: selection scans the bitmap instead."""
+    data = G.uniform_bytes(1 << 20, seed=8)
+    ends, dg = run_cdc(hg, data, mask_bits=2, magic=1, min_chunk=64, max_chunk=4096)
+    cands = oracle.window_candidates(data, 20, 2, 1, nthreads=8)
+    assert cands.size > (1 << 20) // 128 + 4096
+    assert np.array_equal(ends, oracle.select(cands, data.size, 64, 4096))
+    assert np.array_equal(dg, oracle.hash_chunks(oracle.MD5, data, ends))
+
+
+def test_cdc_constant_input(hg):
+    for v in range(256):
+        if oracle.window_candidates(bytes([v]) * 20, 20, 13, 0x0F0F).size == 0:
+            break
+    data = np.full(1_000_000, v, np.uint8)
+    ends, _ = run_cdc(hg, data)
+    assert ends.tolist() == list(range(65536, 1_000_000, 65536)) + [1_000_000]
+
+
+@pytest.mark.parametrize("algo", [oracle.MD5, oracle.SHA1])
+def test_hash_chunks_arbitrary(hg, algo):
+    import paper_1202_3669_b300 as hgb
+    data = G.uniform_bytes(300_000, seed=4)
+    g = G.rng(5)
+    ends = np.unique(np.concatenate([g.integers(1, 300_000, 300), [300_000, 1, 2, 3, 64, 65, 128]]))
+    d = to_device(data, 3)
+    e = torch.from_numpy(ends.astype(np.int64)).cuda()
+    dg = hg.hash_chunks(d, e, algo)
+    hg.sync()
+    assert np.array_equal(dg.cpu().numpy(), oracle.hash_chunks(algo, data, ends.astype(np.uint64)))
+
+
+def test_boundaries_capacity_reports_count(hg):
+    data = G.uniform_bytes(1 << 20, seed=12)
+    want = oracle.cdc(data, nthreads=8)
+    ends, cnt = hg.cdc_boundaries(to_device(data), cap=5)
+    assert int(cnt.item()) == want.size > 5
+    assert np.array_equal(ends[:5].cpu().numpy().astype(np.uint64), want[:5])
+    hg.sync()
+
+
+@pytest.fixture(scope="module")
+def versions():
+    base = G.uniform_bytes(64 << 20, seed=2)
+    v2, _ = G.edited_version(base, seed=3)
+    return base, v2
+
+
+def test_config_cdc_two_versions(hg, versions):
+    """64 MiB base + 1%-edited second version: boundaries, MD5 digests, shared fraction."""
+    out = []
+    for v in versions:
+        ends, dg = run_cdc(hg, v)
+        cands = oracle.window_candidates(v, 20, 13, 0x0F0F, nthreads=16)
+        want = oracle.select(cands, v.size, 2048, 65536)
+        assert np.array_equal(ends, want)
+        check_chunking(want.tolist(), cands.tolist(), v.size, 2048, 65536)
+        assert np.array_equal(dg, oracle.hash_chunks(oracle.MD5, v, want))
+        out.append((ends, dg))
+    frac = oracle.shared_fraction(out[0][0], out[0][1], out[1][0], out[1][1])
+    assert 0.3 < frac < 0.99
