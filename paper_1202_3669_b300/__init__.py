@@ -67,8 +67,8 @@ class Context:
                     out: torch.Tensor | None = None, root_out: torch.Tensor | None = None,
                     stream=None):
         n = data.numel()
-        nblk = (n + block - 1) // block
-        dl = DIGEST_LEN[algo]
+        nblk = (n + block - 1) // block if block > 0 else 0
+        dl = DIGEST_LEN.get(algo, 16)
         if out is None:
             out = torch.empty((nblk, dl), dtype=torch.uint8, device=self.device)
         if root and root_out is None:
