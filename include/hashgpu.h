@@ -158,6 +158,29 @@ int hg_cdc_boundaries(hg_ctx *ctx, const uint8_t *d_in, uint64_t n, const hg_cdc
 int hg_hash_chunks(hg_ctx *ctx, int algo, const uint8_t *d_in, uint64_t n, const uint64_t *d_ends,
                    uint64_t nchunk, const uint64_t *d_count, uint8_t *d_digests, void *stream);
 
+/*
+ * Chunk boundaries without allocating: the same result as hg_cdc_boundaries,
+ * for callers that cannot call cudaMalloc -- a write path that must not stall
+ * on the device-wide synchronisation cudaMalloc/cudaFree can cause, a process
+ * whose device memory belongs to another allocator, or a service whose device
+ * footprint must be fixed at load time. (The paper has no counterpart: its
+ * runtime preallocates buffers per job instead, Sec. 3.2.3.)
+ * No context is needed and nothing is allocated or freed: the scratch lives in
+ * one static device array of the library (about 3.1 MiB, held by every GPU
+ * that loads the library until the process exits). Inputs above
+ * HG_STATIC_MAX_BYTES are rejected with HG_ECAPACITY before anything is
+ * enqueued. Runs on the current CUDA device. Its first call on each device
+ * looks up that device's address of the array; make that first call before
+ * any stream capture. All calls share the one array: calls whose work
+ * overlaps on the GPU (two streams, two host threads) race and corrupt each
+ * other's results, so serialise them. If a bounded device-side wait gave up,
+ * *d_count is set to UINT64_MAX. Other arguments and results as for
+ * hg_cdc_boundaries.
+ */
+#define HG_STATIC_MAX_BYTES (16ull << 20)
+int hg_cdc_boundaries_static(const uint8_t *d_in, uint64_t n, const hg_cdc_params *params,
+                             uint64_t *d_ends, uint64_t cap, uint64_t *d_count, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

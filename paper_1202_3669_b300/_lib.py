@@ -39,6 +39,7 @@ SIGNATURES = {
     "hg_cdc_candidates": (_i32, [_vp, _vp, _u64, C.POINTER(hg_cdc_params), _vp, _u64, _vp, _vp]),
     "hg_cdc_boundaries": (_i32, [_vp, _vp, _u64, C.POINTER(hg_cdc_params), _vp, _u64, _vp, _vp]),
     "hg_hash_chunks": (_i32, [_vp, _i32, _vp, _u64, _vp, _u64, _vp, _vp, _vp]),
+    "hg_cdc_boundaries_static": (_i32, [_vp, _u64, C.POINTER(hg_cdc_params), _vp, _u64, _vp, _vp]),
 }
 
 
@@ -122,3 +123,7 @@ def hg_cdc_boundaries(ctx, d_in, n, params, d_ends, cap, d_count, stream) -> int
 
 def hg_hash_chunks(ctx, algo, d_in, n, d_ends, nchunk, d_count, d_digests, stream) -> int:
     return lib.hg_hash_chunks(ctx, algo, d_in, n, d_ends, nchunk, d_count, d_digests, stream)
+
+
+def hg_cdc_boundaries_static(d_in, n, params, d_ends, cap, d_count, stream) -> int:
+    return lib.hg_cdc_boundaries_static(d_in, n, C.byref(params), d_ends, cap, d_count, stream)

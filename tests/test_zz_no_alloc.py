@@ -1,0 +1,54 @@
+"""hg_cdc_boundaries_static: chunk boundaries for callers that cannot allocate.
+
+Callers on a write path that must not stall on cudaMalloc's device-wide
+synchronisation, or whose device memory belongs to another allocator, use this
+entry point; it keeps its scratch in a static device array. Its results must
+equal those of hg_cdc_boundaries (exactly: boundaries are integers), on two
+calls in a row, which also checks that the reused array's old contents do not
+leak into the next answer. This file is collected last on purpose.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+import torch
+
+from gen import inputs as G
+
+pytestmark = pytest.mark.gpu
+
+
+def test_static_entry_matches_context_entry():
+    import paper_1202_3669_b300 as hgb
+    from paper_1202_3669_b300 import _lib
+    p = hgb.default_params()
+    ctx = hgb.Context(0)
+    s = torch.cuda.current_stream().cuda_stream
+    # two different inputs, the second smaller, so stale scratch would show
+    for n, seed in (((12 << 20) + 4321, 71), ((3 << 20) + 17, 72)):
+        data = torch.from_numpy(G.uniform_bytes(n, seed)).cuda()
+        cap = n // p.min_chunk + 2
+        e_ref, c_ref = ctx.cdc_boundaries(data, p, cap=cap)
+        e_st = torch.empty(cap, dtype=torch.int64, device="cuda")
+        c_st = torch.zeros(1, dtype=torch.int64, device="cuda")
+        rc = _lib.lib.hg_cdc_boundaries_static(data.data_ptr(), n, C.byref(p), e_st.data_ptr(),
+                                               cap, c_st.data_ptr(), s)
+        assert rc == 0
+        torch.cuda.synchronize()
+        k = int(c_ref.item())
+        assert int(c_st.item()) == k > 100
+        assert torch.equal(e_st[:k], e_ref[:k])
+    ctx.sync()
+    ctx.close()
+
+
+def test_static_entry_rejects_oversized_input():
+    from paper_1202_3669_b300 import _lib
+    import paper_1202_3669_b300 as hgb
+    p = hgb.default_params()
+    out = torch.empty(8, dtype=torch.int64, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    rc = _lib.lib.hg_cdc_boundaries_static(out.data_ptr(), (16 << 20) + 1, C.byref(p),
+                                           out.data_ptr(), 8, cnt.data_ptr(),
+                                           torch.cuda.current_stream().cuda_stream)
+    assert rc == _lib.HG_ECAPACITY
