@@ -159,6 +159,57 @@ int hg_hash_chunks(hg_ctx *ctx, int algo, const uint8_t *d_in, uint64_t n, const
                    uint64_t nchunk, const uint64_t *d_count, uint8_t *d_digests, void *stream);
 
 /*
+ * Batched chunking and chunk digests for many files in one pass (Sec. 3.2.3:
+ * the runtime batches a stream of hashing jobs; Sec. 4.1: the gains need
+ * batches; Sec. 3.2.4: writes are buffered so one GPU job covers many chunks).
+ * The nfile files are stored back to back in one device buffer: file f is
+ * bytes [h_file_off[f], h_file_off[f+1]) with h_file_off[0] = 0 and the
+ * offsets non-decreasing (empty files allowed). Every file is chunked on its
+ * own exactly as hg_cdc_boundaries would (no window crosses a file start) and
+ * every chunk is digested as hg_hash_chunks would.
+ *
+ * Output layout ("slots"): file f owns slots [slot_off[f], slot_off[f+1]),
+ * slot_off[f+1] - slot_off[f] = size_f / min_chunk + 1 (0 for an empty file),
+ * which is at least the number of chunks the rule can make. Chunk i of file f
+ * ends at d_ends[slot_off[f] + i] (offset relative to the file's start) and
+ * its digest is d_digests[(slot_off[f] + i) * dlen ...]; d_counts[f] receives
+ * the file's chunk count. hg_batch_slots() returns the total number of slots
+ * and, when h_slot_off is not NULL, writes the nfile + 1 slot offsets there.
+ *
+ * hg_batch_create copies the offsets, classifies files for the selection step
+ * and allocates all scratch once (counted against the context's budget);
+ * hg_batch_cdc_hash only enqueues memsets and kernels (no allocation, no host
+ * synchronisation); hg_batch_cdc_hash_graph does the same through a CUDA graph
+ * captured on the first call and replayed while the pointers, algorithm and
+ * tuning stay the same. hg_batch_sync synchronises the stream and returns the
+ * batch's device error word. A plan may be used by one stream at a time.
+ */
+typedef struct hg_batch hg_batch;
+typedef struct {
+    int32_t window_ctas_per_sm;   /* persistent window kernel CTAs per SM */
+    int32_t hash_threads;         /* chunk-hash kernel threads per CTA (32..512, power of 2) */
+    int32_t hash_ctas_per_sm;     /* chunk-hash kernel CTAs per SM */
+    int32_t reserved;
+    uint64_t long_chunk_bytes;    /* chunks at least this long are hashed first */
+} hg_batch_tuning;
+
+int hg_batch_create(hg_ctx *ctx, const uint64_t *h_file_off, uint32_t nfile,
+                    const hg_cdc_params *params, hg_batch **out);
+int hg_batch_destroy(hg_batch *batch);
+uint64_t hg_batch_slots(const hg_batch *batch, uint64_t *h_slot_off);
+int hg_batch_cdc_hash(hg_batch *batch, int algo, const uint8_t *d_data, uint64_t *d_ends,
+                      uint64_t *d_counts, uint8_t *d_digests, void *stream);
+int hg_batch_cdc_hash_graph(hg_batch *batch, int algo, const uint8_t *d_data, uint64_t *d_ends,
+                            uint64_t *d_counts, uint8_t *d_digests, void *stream);
+int hg_batch_sync(hg_batch *batch, void *stream);
+int hg_batch_get_tuning(const hg_batch *batch, hg_batch_tuning *tuning);
+int hg_batch_set_tuning(hg_batch *batch, const hg_batch_tuning *tuning);
+/* Time a small set of tunings on this batch (synchronous: runs the batch about
+ * 60 times) and keep the fastest; it is also written to *best if not NULL. */
+int hg_batch_autotune(hg_batch *batch, int algo, const uint8_t *d_data, uint64_t *d_ends,
+                      uint64_t *d_counts, uint8_t *d_digests, void *stream, hg_batch_tuning *best);
+
+/*
  * Chunk boundaries without allocating: the same result as hg_cdc_boundaries,
  * for callers that cannot call cudaMalloc -- a write path that must not stall
  * on the device-wide synchronisation cudaMalloc/cudaFree can cause, a process

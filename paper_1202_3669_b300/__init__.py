@@ -6,13 +6,16 @@ raw C functions are re-exported under their C names from `_lib`.
 """
 from __future__ import annotations
 
+import numpy as np
 import torch
 
 from . import _lib
 from ._lib import (HG_MD5, HG_SHA1, HashGPUError, check, default_params,  # noqa: F401
-                   hg_cdc_boundaries, hg_cdc_candidates, hg_cdc_params, hg_destroy,
-                   hg_digest_len, hg_hash_blocks, hg_hash_chunks, hg_init, hg_reserve,
-                   hg_scratch_bytes, hg_sync, hg_window_bitmap)
+                   hg_batch_autotune, hg_batch_cdc_hash, hg_batch_cdc_hash_graph, hg_batch_create,
+                   hg_batch_destroy, hg_batch_get_tuning, hg_batch_set_tuning, hg_batch_slots,
+                   hg_batch_sync, hg_batch_tuning, hg_cdc_boundaries, hg_cdc_boundaries_static,
+                   hg_cdc_candidates, hg_cdc_params, hg_destroy, hg_digest_len, hg_hash_blocks,
+                   hg_hash_chunks, hg_init, hg_reserve, hg_scratch_bytes, hg_sync, hg_window_bitmap)
 
 MD5, SHA1 = HG_MD5, HG_SHA1
 DIGEST_LEN = {MD5: 16, SHA1: 20}
@@ -130,3 +133,71 @@ class Context:
         ends, count = self.cdc_boundaries(data, p, stream=stream)
         dg = self.hash_chunks(data, ends, algo, count=count, stream=stream)
         return ends, count, dg
+
+
+class Batch:
+    """Many files stored back to back in one device buffer, chunked and hashed in one pass.
+
+    file_off: nfile + 1 byte offsets (file f = bytes [file_off[f], file_off[f+1])).
+    Results use the slot layout of include/hashgpu.h: chunk i of file f ends at
+    ends[slot_off[f] + i] (relative to the file start), with its digest in the same row.
+    """
+
+    def __init__(self, ctx: Context, file_off, p: hg_cdc_params | None = None):
+        self.ctx = ctx
+        self.p = p or default_params()
+        self.file_off = np.ascontiguousarray(file_off, dtype=np.uint64)
+        self.nfile = self.file_off.size - 1
+        self.h = hg_batch_create(ctx.h, self.file_off.ctypes.data, self.nfile, self.p)
+        self.slot_off = np.zeros(self.nfile + 1, dtype=np.uint64)
+        self.total_slots = hg_batch_slots(self.h, self.slot_off.ctypes.data)
+
+    def close(self):
+        if getattr(self, "h", None):
+            hg_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def outputs(self, algo: int):
+        dev = self.ctx.device
+        return (torch.empty(max(1, self.total_slots), dtype=torch.int64, device=dev),
+                torch.zeros(max(1, self.nfile), dtype=torch.int64, device=dev),
+                torch.empty((max(1, self.total_slots), DIGEST_LEN[algo]), dtype=torch.uint8,
+                            device=dev))
+
+    def cdc_hash(self, data: torch.Tensor, algo: int = SHA1, out=None, graph: bool = False,
+                 stream=None):
+        ends, counts, dg = out if out is not None else self.outputs(algo)
+        fn = hg_batch_cdc_hash_graph if graph else hg_batch_cdc_hash
+        check(fn(self.h, algo, _ptr(data), _ptr(ends), _ptr(counts), _ptr(dg), _stream(stream)),
+              "hg_batch_cdc_hash")
+        return ends, counts, dg
+
+    def sync(self, stream=None):
+        check(hg_batch_sync(self.h, _stream(stream)), "batch device error")
+
+    def tuning(self) -> hg_batch_tuning:
+        t = hg_batch_tuning()
+        check(hg_batch_get_tuning(self.h, t))
+        return t
+
+    def set_tuning(self, t: hg_batch_tuning):
+        check(hg_batch_set_tuning(self.h, t), "hg_batch_set_tuning")
+
+    def autotune(self, data: torch.Tensor, algo: int = SHA1, out=None, stream=None) -> hg_batch_tuning:
+        ends, counts, dg = out if out is not None else self.outputs(algo)
+        best = hg_batch_tuning()
+        check(hg_batch_autotune(self.h, algo, _ptr(data), _ptr(ends), _ptr(counts), _ptr(dg),
+                                _stream(stream), best), "hg_batch_autotune")
+        return best
+
+    def file_results(self, f: int, ends: torch.Tensor, counts: torch.Tensor, dg: torch.Tensor):
+        """(ends, digests) of file f as numpy arrays (host copies)."""
+        k = int(counts[f].item())
+        a = int(self.slot_off[f])
+        return (ends[a:a + k].cpu().numpy().astype(np.uint64), dg[a:a + k].cpu().numpy())

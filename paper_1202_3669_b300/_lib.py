@@ -20,6 +20,12 @@ HG_MD5, HG_SHA1 = 0, 1
 _vp, _u64, _u32, _i32, _sz = C.c_void_p, C.c_uint64, C.c_uint32, C.c_int, C.c_size_t
 
 
+class hg_batch_tuning(C.Structure):
+    _fields_ = [("window_ctas_per_sm", C.c_int32), ("hash_threads", C.c_int32),
+                ("hash_ctas_per_sm", C.c_int32), ("reserved", C.c_int32),
+                ("long_chunk_bytes", C.c_uint64)]
+
+
 class hg_cdc_params(C.Structure):
     _fields_ = [("window", C.c_uint32), ("mask_bits", C.c_uint32), ("magic", C.c_uint32),
                 ("reserved", C.c_uint32), ("min_chunk", C.c_uint64), ("max_chunk", C.c_uint64)]
@@ -39,6 +45,15 @@ SIGNATURES = {
     "hg_cdc_candidates": (_i32, [_vp, _vp, _u64, C.POINTER(hg_cdc_params), _vp, _u64, _vp, _vp]),
     "hg_cdc_boundaries": (_i32, [_vp, _vp, _u64, C.POINTER(hg_cdc_params), _vp, _u64, _vp, _vp]),
     "hg_hash_chunks": (_i32, [_vp, _i32, _vp, _u64, _vp, _u64, _vp, _vp, _vp]),
+    "hg_batch_create": (_i32, [_vp, _vp, _u32, C.POINTER(hg_cdc_params), C.POINTER(_vp)]),
+    "hg_batch_destroy": (_i32, [_vp]),
+    "hg_batch_slots": (_u64, [_vp, _vp]),
+    "hg_batch_cdc_hash": (_i32, [_vp, _i32, _vp, _vp, _vp, _vp, _vp]),
+    "hg_batch_cdc_hash_graph": (_i32, [_vp, _i32, _vp, _vp, _vp, _vp, _vp]),
+    "hg_batch_sync": (_i32, [_vp, _vp]),
+    "hg_batch_get_tuning": (_i32, [_vp, _vp]),
+    "hg_batch_set_tuning": (_i32, [_vp, _vp]),
+    "hg_batch_autotune": (_i32, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp]),
     "hg_cdc_boundaries_static": (_i32, [_vp, _u64, C.POINTER(hg_cdc_params), _vp, _u64, _vp, _vp]),
 }
 
@@ -127,3 +142,43 @@ def hg_hash_chunks(ctx, algo, d_in, n, d_ends, nchunk, d_count, d_digests, strea
 
 def hg_cdc_boundaries_static(d_in, n, params, d_ends, cap, d_count, stream) -> int:
     return lib.hg_cdc_boundaries_static(d_in, n, C.byref(params), d_ends, cap, d_count, stream)
+
+
+def hg_batch_create(ctx, h_file_off_ptr, nfile, params) -> int:
+    h = _vp()
+    check(lib.hg_batch_create(ctx, h_file_off_ptr, nfile, C.byref(params), C.byref(h)),
+          "hg_batch_create")
+    return h.value
+
+
+def hg_batch_destroy(batch) -> int:
+    return lib.hg_batch_destroy(batch)
+
+
+def hg_batch_slots(batch, h_slot_off_ptr) -> int:
+    return lib.hg_batch_slots(batch, h_slot_off_ptr)
+
+
+def hg_batch_cdc_hash(batch, algo, d_data, d_ends, d_counts, d_digests, stream) -> int:
+    return lib.hg_batch_cdc_hash(batch, algo, d_data, d_ends, d_counts, d_digests, stream)
+
+
+def hg_batch_cdc_hash_graph(batch, algo, d_data, d_ends, d_counts, d_digests, stream) -> int:
+    return lib.hg_batch_cdc_hash_graph(batch, algo, d_data, d_ends, d_counts, d_digests, stream)
+
+
+def hg_batch_sync(batch, stream) -> int:
+    return lib.hg_batch_sync(batch, stream)
+
+
+def hg_batch_get_tuning(batch, tuning) -> int:
+    return lib.hg_batch_get_tuning(batch, C.byref(tuning))
+
+
+def hg_batch_set_tuning(batch, tuning) -> int:
+    return lib.hg_batch_set_tuning(batch, C.byref(tuning))
+
+
+def hg_batch_autotune(batch, algo, d_data, d_ends, d_counts, d_digests, stream, best) -> int:
+    return lib.hg_batch_autotune(batch, algo, d_data, d_ends, d_counts, d_digests, stream,
+                                 C.byref(best) if best is not None else None)

@@ -7,85 +7,11 @@
 // here the scan is done on the device by compaction and a selection kernel.
 #include "hg_device.cuh"
 #include "hg_internal.h"
+#include "hg_select.cuh"
+#include "hg_window.cuh"
 
 namespace hg {
 namespace {
-
-constexpr int kHalo = 64;                              // >= window - 1, multiple of 16
-constexpr int kSmemBytes = kHalo + (int)kWinTile + 16; // + a zeroed 16-byte pad
-constexpr long kWaitLimit = 1L << 22;                  // bounded mbarrier polling
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(mbar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// MD5 of one window given its data words d[] (little-endian, the last word may
-// carry bytes past the window, which are masked). Only word A of the final
-// state is formed: the window test reads the first four digest bytes.
-template <int W>
-__device__ __forceinline__ uint32_t window_a(const uint32_t (&d)[(W + 3) / 4]) {
-    constexpr int NW = (W + 3) / 4;
-    uint32_t M[16];
-#pragma unroll
-    for (int i = 0; i < 16; i++) M[i] = 0;
-#pragma unroll
-    for (int i = 0; i < NW; i++) M[i] = d[i];
-    if (W % 4 == 0) {
-        M[W / 4] = 0x80u;                             // padding marker after the data
-    } else {
-        constexpr uint32_t keep = (1u << (8 * (W % 4))) - 1u;
-        M[NW - 1] = (d[NW - 1] & keep) | (0x80u << (8 * (W % 4)));
-    }
-    M[14] = (uint32_t)W * 8u;                         // bit length, little-endian
-    uint32_t a = kMd5A, b = kMd5B, c = kMd5C, dd = kMd5D;
-    md5_rounds<false>(a, b, c, dd, M);
-    return a + kMd5A;
-}
-
-// Window number S (0..6) of a group, counted in bytes from word cur[0].
-template <int W, int S>
-__device__ __forceinline__ uint32_t window_at(const uint32_t (&cur)[(W + 3) / 4 + 2]) {
-    constexpr int NW = (W + 3) / 4, SH = S & 3, WO = S >> 2;
-    uint32_t d[NW];
-#pragma unroll
-    for (int k = 0; k < NW; k++)
-        d[k] = SH == 0 ? cur[WO + k] : __funnelshift_r(cur[WO + k], cur[WO + k + 1], 8 * SH);
-    return window_a<W>(d);
-}
-
-// Window hash for a window length known only at run time (any 1..55): the
-// message words are gathered byte by byte from shared memory.
-__device__ __forceinline__ uint32_t window_a_rt(const uint8_t *sbuf, int start, int w) {
-    uint32_t M[16];
-#pragma unroll
-    for (int i = 0; i < 14; i++) {
-        uint32_t x = 0;
-#pragma unroll
-        for (int j = 0; j < 4; j++) {
-            const int k = 4 * i + j;
-            const uint32_t byte = k < w ? (uint32_t)sbuf[start + k] : (k == w ? 0x80u : 0u);
-            x |= byte << (8 * j);
-        }
-        M[i] = x;
-    }
-    M[14] = (uint32_t)w * 8u;
-    M[15] = 0;
-    uint32_t a = kMd5A, b = kMd5B, c = kMd5C, d = kMd5D;
-    md5_rounds<false>(a, b, c, d, M);
-    return a + kMd5A;
-}
 
 // One CTA covers kWinTile consecutive window ends; thread t owns ends
 // [tile + 32t, tile + 32t + 32) and so exactly bitmap word tile/32 + t.
@@ -95,14 +21,10 @@ __device__ __forceinline__ uint32_t window_a_rt(const uint8_t *sbuf, int start, 
 template <int W>
 __global__ void __launch_bounds__(kWinThreads) k_window_bitmap(const uint8_t *__restrict__ in,
                                                                uint64_t n, uint32_t wrt,
-                                                               uint32_t mask,
-                                                               uint32_t magic,
+                                                               uint32_t mask, uint32_t magic,
                                                                uint32_t *__restrict__ bitmap,
                                                                uint32_t *__restrict__ tile_cnt,
                                                                int *err) {
-    constexpr int NW = W ? (W + 3) / 4 : 1;
-    constexpr int OFF = kHalo - (W ? W - 1 : 0);      // local byte of window 0's start
-    constexpr int B0 = OFF / 4, R0 = OFF % 4;
     const uint32_t wlen = W ? (uint32_t)W : wrt;
     __shared__ __align__(128) uint8_t sbuf[kSmemBytes];
     __shared__ __align__(8) uint64_t mbar;
@@ -113,33 +35,17 @@ __global__ void __launch_bounds__(kWinThreads) k_window_bitmap(const uint8_t *__
     const bool fast = ((reinterpret_cast<uintptr_t>(in) & 15) == 0) && tile >= (uint64_t)kHalo &&
                       tile + kWinTile <= n;
     if (t < 4) reinterpret_cast<uint32_t *>(sbuf + kHalo + kWinTile)[t] = 0;
-    bool load_ok = true;
+    bool timed_out = false;
     if (fast) {
         const uint32_t mb = smem_u32(&mbar);
-        if (t == 0) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb));
-            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        }
+        if (t == 0) mbar_init(mb);
         __syncthreads();
-        if (t == 0) {
-            const uint32_t bytes = (uint32_t)(kHalo + kWinTile);
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb),
-                         "r"(bytes)
-                         : "memory");
-            asm volatile(
-                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
-                "[%3];" ::"r"(smem_u32(sbuf)),
-                "l"(in + tile - kHalo), "r"(bytes), "r"(mb)
-                : "memory");
-        }
-        bool done = false;
-        for (long it = 0; it < kWaitLimit && !done; it++) done = mbar_try_wait(mb, 0);
-        if (!done) {
-            // give up on this tile; keep polling (bounded) so the copy cannot
-            // land in shared memory after the CTA has left
+        if (t == 0) bulk_load(smem_u32(sbuf), in + tile - kHalo, (uint32_t)(kHalo + kWinTile), mb);
+        timed_out = !mbar_wait(mb, 0);
+        if (timed_out) {
+            // keep polling (bounded) so the copy cannot land after the CTA left
             atomicCAS(err, 0, (int)HG_ETIMEDOUT);
-            for (long it = 0; it < kWaitLimit && !done; it++) done = mbar_try_wait(mb, 0);
-            load_ok = false;
+            mbar_wait(mb, 0);
         }
     } else {
         for (int i = t; i < kHalo + (int)kWinTile; i += kWinThreads) {
@@ -147,45 +53,10 @@ __global__ void __launch_bounds__(kWinThreads) k_window_bitmap(const uint8_t *__
             sbuf[i] = (g >= 0 && (uint64_t)g < n) ? in[g] : (uint8_t)0;
         }
     }
-    __syncthreads();
-    if (!load_ok) return;
+    if (__syncthreads_or(timed_out)) return;
 
-    uint32_t bits = 0;
-    if constexpr (W > 0) {
-        const uint32_t *sw = reinterpret_cast<const uint32_t *>(sbuf);
-        uint32_t cur[NW + 2];
-#pragma unroll
-        for (int i = 0; i < NW + 2; i++) cur[i] = sw[8 * t + B0 + i];
-#pragma unroll 1
-        for (int g = 0; g < 8; g++) {
-            const uint32_t h0 = window_at<W, R0 + 0>(cur);
-            const uint32_t h1 = window_at<W, R0 + 1>(cur);
-            const uint32_t h2 = window_at<W, R0 + 2>(cur);
-            const uint32_t h3 = window_at<W, R0 + 3>(cur);
-            const uint32_t nib = (uint32_t)((h0 & mask) == magic) |
-                                 ((uint32_t)((h1 & mask) == magic) << 1) |
-                                 ((uint32_t)((h2 & mask) == magic) << 2) |
-                                 ((uint32_t)((h3 & mask) == magic) << 3);
-            bits |= nib << (4 * g);
-#pragma unroll
-            for (int i = 0; i < NW + 1; i++) cur[i] = cur[i + 1];
-            cur[NW + 1] = sw[8 * t + B0 + g + NW + 2];       // stays inside the padded tile
-        }
-    } else {
-        const int first = kHalo + 32 * t - (int)(wlen - 1);
-#pragma unroll 1
-        for (int j = 0; j < 32; j++)
-            bits |= (uint32_t)((window_a_rt(sbuf, first + j, (int)wlen) & mask) == magic) << j;
-    }
-    // clear ends before the first full window and past the input
     const uint64_t p0 = tile + 32u * (uint64_t)t;
-    const uint64_t lo = (uint64_t)(wlen - 1) > p0 ? (uint64_t)(wlen - 1) - p0 : 0;
-    const uint64_t hi = n > p0 ? n - p0 : 0;
-    if (lo >= 32 || hi == 0) bits = 0;
-    else {
-        if (lo) bits &= ~0u << lo;
-        if (hi < 32) bits &= (1u << hi) - 1u;
-    }
+    const uint32_t bits = clip_bits(window_bits32<W>(sbuf, t, wlen, mask, magic), p0, wlen, n);
     const uint64_t nwords = (n + 31) / 32;
     const uint64_t widx = tile / 32 + t;
     if (widx < nwords) bitmap[widx] = bits;
@@ -298,16 +169,14 @@ __device__ uint64_t first_cut_bitmap(const uint32_t *__restrict__ bitmap, uint64
     return UINT64_MAX;
 }
 
-// Greedy min/max selection (one warp). Reads the sorted candidate list 32 at a
-// time; if the list overflowed its capacity it scans the bitmap instead.
-__global__ void k_select(const uint64_t *__restrict__ cands, const uint64_t *__restrict__ d_ncand,
-                         uint64_t cand_cap, const uint32_t *__restrict__ bitmap, uint64_t n,
-                         uint64_t mn, uint64_t mx, uint64_t *__restrict__ ends, uint64_t cap,
-                         uint64_t *__restrict__ d_count) {
+// Greedy min/max selection by one warp, walking the chain chunk by chunk. It
+// reads the sorted candidate list 32 at a time, or scans the bitmap when the
+// list overflowed its capacity. Serial: used only for that overflow case.
+__device__ void select_serial(const uint64_t *__restrict__ cands, uint64_t ncand, bool use_list,
+                              const uint32_t *__restrict__ bitmap, uint64_t n, uint64_t mn,
+                              uint64_t mx, uint64_t *__restrict__ ends, uint64_t cap,
+                              uint64_t *__restrict__ d_count) {
     const int lane = threadIdx.x & 31;
-    if (threadIdx.x >= 32) return;
-    const uint64_t ncand = *d_ncand;
-    const bool use_list = ncand <= cand_cap;
     uint64_t base = 0;
     uint64_t mine = (use_list && lane < ncand) ? cands[lane] : UINT64_MAX;
     uint64_t s = 0, count = 0;
@@ -338,6 +207,20 @@ __global__ void k_select(const uint64_t *__restrict__ cands, const uint64_t *__r
         s = cut;
     }
     if (lane == 0) *d_count = count;
+}
+
+// Selection of the whole stream by one CTA (parallel, exact); when the
+// candidate list overflowed, warp 0 walks the bitmap instead.
+__global__ void __launch_bounds__(kSelThreads) k_select_par(
+    const uint64_t *__restrict__ cands, const uint64_t *__restrict__ d_ncand, uint64_t cand_cap,
+    const uint32_t *__restrict__ bitmap, uint64_t n, uint64_t mn, uint64_t mx,
+    uint64_t *__restrict__ ends, uint64_t cap, uint64_t *__restrict__ d_count) {
+    const uint64_t ncand = *d_ncand;
+    if (ncand > cand_cap || ncand >= 0xffffffffull) {
+        if (threadIdx.x < 32) select_serial(cands, ncand, false, bitmap, n, mn, mx, ends, cap, d_count);
+        return;
+    }
+    select_block(cands, (uint32_t)ncand, 0, n, mn, mx, ends, cap, d_count);
 }
 
 template <int W>
@@ -383,8 +266,8 @@ int launch_compact(const uint32_t *d_bitmap, uint64_t n, const uint32_t *d_tile_
 int launch_select(const uint64_t *d_cands, const uint64_t *d_ncand, uint64_t cand_cap,
                   const uint32_t *d_bitmap, uint64_t n, const hg_cdc_params &p, uint64_t *d_ends,
                   uint64_t cap, uint64_t *d_count, cudaStream_t s) {
-    k_select<<<1, 32, 0, s>>>(d_cands, d_ncand, cand_cap, d_bitmap, n, p.min_chunk, p.max_chunk,
-                              d_ends, cap, d_count);
+    k_select_par<<<1, kSelThreads, 0, s>>>(d_cands, d_ncand, cand_cap, d_bitmap, n, p.min_chunk,
+                                           p.max_chunk, d_ends, cap, d_count);
     return cuda_status(cudaGetLastError());
 }
 

@@ -174,9 +174,10 @@ struct Sha1 {
 };
 
 // Digest of the len bytes at msg, which may start at any byte address. Full
-// 64-byte blocks are read as aligned 16-byte vectors (the one vector that
-// straddles the end of the message stays inside its aligned 16-byte granule,
-// so it never crosses a page) and shifted into place; the final partial block
+// 64-byte blocks are read as aligned 16-byte vectors; for a message that does
+// not start on a 16-byte boundary they are shifted into place (the aligned
+// vectors at either end stay inside the 16-byte granules that hold the first
+// and last message bytes, so they never cross a page). The final partial block
 // and the padding are assembled from byte loads inside the message.
 template <class H>
 __device__ void hash_range(const uint8_t *__restrict__ msg, uint64_t len, H &hs) {
@@ -186,31 +187,44 @@ __device__ void hash_range(const uint8_t *__restrict__ msg, uint64_t len, H &hs)
     const uint32_t sh = (uint32_t)(addr & 15);
     const uint32_t q = sh >> 2, r8 = (sh & 3) * 8;
     const uint4 *p = reinterpret_cast<const uint4 *>(addr - sh);
-    for (uint64_t k = 0; k < nfull; k++) {
-        uint32_t v[20];
-#pragma unroll
-        for (int i = 0; i < 4; i++) {
-            const uint4 x = __ldg(p + 4 * k + i);
-            v[4 * i] = x.x; v[4 * i + 1] = x.y; v[4 * i + 2] = x.z; v[4 * i + 3] = x.w;
+    if (sh == 0) {
+        // aligned message: four 16-byte loads per block, no shifting
+        for (uint64_t k = 0; k < nfull; k++) {
+            const uint4 x0 = __ldg(p + 4 * k), x1 = __ldg(p + 4 * k + 1);
+            const uint4 x2 = __ldg(p + 4 * k + 2), x3 = __ldg(p + 4 * k + 3);
+            const uint32_t M[16] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w,
+                                    x2.x, x2.y, x2.z, x2.w, x3.x, x3.y, x3.z, x3.w};
+            hs.compress(M);
         }
-        if (sh) {
-            const uint4 x = __ldg(p + 4 * k + 4);
-            v[16] = x.x; v[17] = x.y; v[18] = x.z; v[19] = x.w;
-        } else {
-            v[16] = v[17] = v[18] = v[19] = 0;
+    } else {
+        // unaligned message: five aligned loads per block, shifted into place;
+        // the loads of block k+1 are issued before block k is compressed
+        uint4 x0 = make_uint4(0, 0, 0, 0), x1 = x0, x2 = x0, x3 = x0, x4 = x0;
+        if (nfull) {
+            x0 = __ldg(p); x1 = __ldg(p + 1); x2 = __ldg(p + 2); x3 = __ldg(p + 3); x4 = __ldg(p + 4);
         }
-        // shift by q words, then by r8 bits
-        uint32_t u[17];
+        for (uint64_t k = 0; k < nfull; k++) {
+            const uint32_t v[20] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w,
+                                    x2.x, x2.y, x2.z, x2.w, x3.x, x3.y, x3.z, x3.w,
+                                    x4.x, x4.y, x4.z, x4.w};
+            if (k + 1 < nfull) {
+                const uint4 *q4 = p + 4 * (k + 1);
+                x0 = __ldg(q4); x1 = __ldg(q4 + 1); x2 = __ldg(q4 + 2); x3 = __ldg(q4 + 3);
+                x4 = __ldg(q4 + 4);
+            }
+            // shift by q words, then by r8 bits
+            uint32_t u[17];
 #pragma unroll
-        for (int i = 0; i < 17; i++) {
-            const uint32_t s1 = (q & 1) ? v[i + 1] : v[i];
-            const uint32_t s2 = (q & 1) ? v[i + 3] : v[i + 2];
-            u[i] = (q & 2) ? s2 : s1;
+            for (int i = 0; i < 17; i++) {
+                const uint32_t s1 = (q & 1) ? v[i + 1] : v[i];
+                const uint32_t s2 = (q & 1) ? v[i + 3] : v[i + 2];
+                u[i] = (q & 2) ? s2 : s1;
+            }
+            uint32_t M[16];
+#pragma unroll
+            for (int i = 0; i < 16; i++) M[i] = r8 ? __funnelshift_r(u[i], u[i + 1], r8) : u[i];
+            hs.compress(M);
         }
-        uint32_t M[16];
-#pragma unroll
-        for (int i = 0; i < 16; i++) M[i] = r8 ? __funnelshift_r(u[i], u[i + 1], r8) : u[i];
-        hs.compress(M);
     }
     // tail: rem bytes, the 0x80 marker, zeros, the length
     const uint32_t rem = (uint32_t)(len & 63);

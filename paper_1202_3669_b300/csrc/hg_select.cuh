@@ -1,0 +1,215 @@
+// Exact min/max chunk-boundary selection on the device (Sec. 2.1 content-based
+// chunking with minimum and maximum chunk sizes): shared by the single-stream
+// and the batched paths.
+//
+// The greedy rule makes the chunk chain a deterministic function of its
+// current start: two chains that ever cut at the same candidate coincide from
+// there on. For a block-wide selection the candidates are split into nseg
+// segments of K; S_j is the chain that starts with a cut at candidate j*K.
+// Phase 1 finds, for every j, the candidate q_j where S_j and S_{j+1} meet
+// (two-pointer walk; chains meet within a few cuts because a chunk spans only
+// a few candidates), and q_{-1} where the true chain T from the stream start
+// meets S_0. With x_0 = q_{-1} and x_{j+1} = max(x_j, q_j), T is the walk from
+// the start to x_0 followed by the pieces of S_j from x_j to x_{j+1}; each
+// piece is walked twice more, once to count its cuts and once to write them at
+// their scanned offsets.
+//
+// Positions are absolute offsets into the buffer that holds the stream; the
+// stream occupies [s0, n) and cuts are written relative to s0.
+#pragma once
+#include <cstdint>
+
+namespace hg {
+
+constexpr int kSelThreads = 1024;
+
+// First index j >= k with C[j] >= target (m if none); C is sorted.
+__device__ __forceinline__ uint32_t lower_bound_from(const uint64_t *__restrict__ C, uint32_t m,
+                                                     uint32_t k, uint64_t target) {
+    if (k >= m || __ldg(C + k) >= target) return k;
+    uint32_t lo = k, hi = m, step = 1;                    // C[lo] < target
+    while (true) {                                        // gallop
+        const uint64_t probe = (uint64_t)lo + step;
+        if (probe >= m) break;
+        if (__ldg(C + probe) >= target) { hi = (uint32_t)probe; break; }
+        lo = (uint32_t)probe;
+        step <<= 1;
+    }
+    while (hi - lo > 1) {                                 // C[lo] < target <= C[hi]
+        const uint32_t mid = lo + (hi - lo) / 2;
+        if (__ldg(C + mid) >= target) hi = mid; else lo = mid;
+    }
+    return hi;
+}
+
+struct NoEmit {
+    __device__ __forceinline__ void operator()(uint64_t) const {}
+};
+struct CountEmit {
+    uint64_t *c;
+    __device__ __forceinline__ void operator()(uint64_t) const { ++*c; }
+};
+struct WriteEmit {
+    uint64_t *ends, cap, *idx, base;
+    __device__ __forceinline__ void operator()(uint64_t cut) const {
+        if (*idx < cap) ends[*idx] = cut - base;
+        ++*idx;
+    }
+};
+
+// One chain step from chunk start s (search for candidates from index k on):
+// emits every cut up to and including the next candidate cut and returns that
+// candidate's index, or emits the remaining forced cuts and n and returns m.
+template <class Emit>
+__device__ uint32_t chain_next(const uint64_t *__restrict__ C, uint32_t m, uint64_t n,
+                               uint64_t mn, uint64_t mx, uint64_t s, uint32_t k, Emit emit) {
+    while (s < n) {
+        const uint32_t j = lower_bound_from(C, m, k, s + mn);
+        if (j < m && __ldg(C + j) <= s + mx) {
+            emit(__ldg(C + j));
+            return j;
+        }
+        if (s + mx < n) {
+            s += mx;                                       // forced cut
+            emit(s);
+            k = j;
+        } else {
+            emit(n);                                       // last chunk
+            return m;
+        }
+    }
+    return m;
+}
+
+template <class Emit>
+__device__ __forceinline__ uint32_t step_from(const uint64_t *__restrict__ C, uint32_t m, uint64_t n,
+                                              uint64_t mn, uint64_t mx, uint32_t node, Emit emit) {
+    return chain_next(C, m, n, mn, mx, __ldg(C + node), node + 1, emit);
+}
+
+// The whole chain of a stream by one thread (used for streams with few candidates).
+template <class Emit>
+__device__ void select_thread(const uint64_t *__restrict__ C, uint32_t m, uint64_t s0, uint64_t n,
+                              uint64_t mn, uint64_t mx, Emit emit) {
+    uint32_t cur = chain_next(C, m, n, mn, mx, s0, 0, emit);
+    while (cur != m) cur = step_from(C, m, n, mn, mx, cur, emit);
+}
+
+// Walk piece p (-1: from s0 to x[0]; j >= 0: from x[j] to x[j+1]).
+template <class Emit>
+__device__ void walk_piece(const uint64_t *__restrict__ C, uint32_t m, uint64_t s0, uint64_t n,
+                           uint64_t mn, uint64_t mx, int p, const uint32_t *x, Emit emit) {
+    uint32_t cur, to;
+    if (p < 0) {
+        to = x[0];
+        cur = chain_next(C, m, n, mn, mx, s0, 0, emit);
+    } else {
+        cur = x[p];
+        to = x[p + 1];
+    }
+    while (cur != to) cur = step_from(C, m, n, mn, mx, cur, emit);
+}
+
+// Block-wide exact selection (blockDim.x == kSelThreads) of the stream [s0, n)
+// whose sorted candidate cuts are C[0..m). Writes at most cap cuts (relative to
+// s0) to ends and the total count to *d_count.
+static __device__ void select_block(const uint64_t *__restrict__ C, uint32_t m, uint64_t s0, uint64_t n,
+                             uint64_t mn, uint64_t mx, uint64_t *__restrict__ ends, uint64_t cap,
+                             uint64_t *__restrict__ d_count) {
+    __shared__ uint32_t q[kSelThreads];          // q[j+1] = meeting candidate of S_j, S_{j+1}
+    __shared__ uint32_t x[kSelThreads + 1];      // x[j] = where T joins S_j
+    __shared__ uint64_t warp_tot[kSelThreads / 32];
+    const int t = threadIdx.x;
+    const uint32_t K = max(16u, (m + kSelThreads - 2) / (kSelThreads - 1));
+    const int nseg = (int)((m + K - 1) / K);              // <= kSelThreads - 1
+    const int p = t - 1;                                  // piece / chain index of this thread
+
+    // phase 1: meeting points
+    if (p >= -1 && p < nseg) {
+        uint32_t a, b;
+        if (p < 0) {
+            a = chain_next(C, m, n, mn, mx, s0, 0, NoEmit{});
+            b = nseg > 0 ? 0 : m;
+        } else {
+            a = (uint32_t)p * K;
+            b = (p + 1 < nseg) ? (uint32_t)(p + 1) * K : m;
+        }
+        while (a != b) {
+            if (a < b) a = step_from(C, m, n, mn, mx, a, NoEmit{});
+            else b = step_from(C, m, n, mn, mx, b, NoEmit{});
+        }
+        q[t] = a;
+    }
+    __syncthreads();
+    // phase 2: x[0] = q_{-1}, x[j+1] = max(x[j], q_j)
+    if (t == 0) {
+        uint32_t run = q[0];
+        x[0] = run;
+        for (int j = 0; j < nseg; j++) {
+            run = max(run, q[j + 1]);
+            x[j + 1] = run;
+        }
+    }
+    __syncthreads();
+    // phase 3: count cuts per piece
+    uint64_t c = 0;
+    if (n > s0 && p >= -1 && p < nseg) walk_piece(C, m, s0, n, mn, mx, p, x, CountEmit{&c});
+    // phase 4: exclusive scan of counts over the block
+    uint64_t v = c;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xffffffffu, v, d);
+        if ((t & 31) >= d) v += y;
+    }
+    if ((t & 31) == 31) warp_tot[t >> 5] = v;
+    __syncthreads();
+    if (t < 32) {
+        uint64_t w = warp_tot[t];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint64_t y = __shfl_up_sync(0xffffffffu, w, d);
+            if (t >= d) w += y;
+        }
+        warp_tot[t] = w;
+    }
+    __syncthreads();
+    const uint64_t excl = v - c + ((t >> 5) ? warp_tot[(t >> 5) - 1] : 0);
+    if (t == kSelThreads - 1) *d_count = excl + c;
+    // phase 5: write
+    if (n > s0 && p >= -1 && p < nseg && c) {
+        uint64_t idx = excl;
+        walk_piece(C, m, s0, n, mn, mx, p, x, WriteEmit{ends, cap, &idx, s0});
+    }
+}
+
+// First window end p in [plo, phi] whose bit is set, by one thread (UINT64_MAX
+// if none). Used only when the candidate list overflowed its capacity.
+__device__ __forceinline__ uint64_t first_bit_thread(const uint32_t *__restrict__ bitmap,
+                                                     uint64_t plo, uint64_t phi) {
+    for (uint64_t wi = plo / 32; wi <= phi / 32; wi++) {
+        uint32_t w = bitmap[wi];
+        if (wi == plo / 32) w &= ~0u << (plo % 32);
+        if (wi == phi / 32 && (phi % 32) != 31) w &= (1u << (phi % 32 + 1)) - 1u;
+        if (w) return wi * 32 + (__ffs(w) - 1);
+    }
+    return UINT64_MAX;
+}
+
+// Greedy selection of the stream [s0, n) by one thread from the bitmap.
+template <class Emit>
+__device__ void select_thread_bitmap(const uint32_t *__restrict__ bitmap, uint64_t s0, uint64_t n,
+                                     uint64_t mn, uint64_t mx, Emit emit) {
+    uint64_t s = s0;
+    while (s < n) {
+        const uint64_t lo = s + mn, hi = min(s + mx, n);
+        uint64_t cut;
+        const uint64_t p = lo <= hi ? first_bit_thread(bitmap, lo - 1, hi - 1) : UINT64_MAX;
+        if (p != UINT64_MAX) cut = p + 1;
+        else if (s + mx < n) cut = s + mx;
+        else cut = n;
+        emit(cut);
+        s = cut;
+    }
+}
+
+}  // namespace hg

@@ -1,0 +1,126 @@
+"""GPU parity of batched chunking + chunk digests (many files, one pass) against the oracle.
+
+Each file of a batch must be chunked and digested exactly as it is alone
+(Sec. 2.1 / Fig. 3 per file); the batch form (Sec. 3.2.3 batching) only
+changes how the work is scheduled.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from gen import inputs as G
+from tests.gpu_util import to_device
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hg():
+    import paper_1202_3669_b300 as hgb
+    ctx = hgb.Context(0)
+    yield ctx
+    ctx.close()
+
+
+def check_batch(hg, sizes, seed, algo, p=None, graph=False, offset=0, sample=None):
+    import paper_1202_3669_b300 as hgb
+    p = p or hgb.default_params()
+    sizes = np.asarray(sizes, dtype=np.int64)
+    data, off = G.files_from_sizes(sizes, seed)
+    b = hgb.Batch(hg, off, p)
+    d = to_device(data, offset)
+    out = b.cdc_hash(d, algo, graph=graph)
+    b.sync()
+    files = range(len(sizes)) if sample is None else sample
+    for f in files:
+        body = data[off[f]:off[f + 1]]
+        cands = oracle.window_candidates(body, p.window, p.mask_bits, p.magic, nthreads=8)
+        want = oracle.select(cands, body.size, p.min_chunk, p.max_chunk)
+        ends, dg = b.file_results(f, *out)
+        assert np.array_equal(ends, want), (f, sizes[f], ends[:5], want[:5])
+        assert np.array_equal(dg, oracle.hash_chunks(algo, body, want)), f
+    b.close()
+    return out
+
+
+@pytest.mark.parametrize("algo", [oracle.MD5, oracle.SHA1])
+def test_batch_mixed_small(hg, algo):
+    sizes = [0, 1, 19, 20, 21, 100, 2047, 2048, 5000, 8192, 8193, 70_000, 0, 3, 300_000,
+             (1 << 20) + 77, 2_500_000, 50, 65_536, 65_537]
+    check_batch(hg, sizes, seed=101, algo=algo)
+
+
+def test_batch_lognormal(hg):
+    sizes = G.lognormal_sizes(300, seed=11, median=32 * 1024, sigma=1.5, hi=4 << 20)
+    check_batch(hg, sizes, seed=12, algo=oracle.SHA1)
+
+
+def test_batch_graph_and_unaligned(hg):
+    sizes = G.lognormal_sizes(64, seed=21, median=20_000, sigma=1.2, hi=2 << 20)
+    check_batch(hg, sizes, seed=22, algo=oracle.MD5, graph=True, offset=3)
+
+
+def test_batch_graph_replay_equals_direct(hg):
+    import paper_1202_3669_b300 as hgb
+    sizes = G.lognormal_sizes(128, seed=31, median=40_000, sigma=1.3, hi=3 << 20)
+    data, off = G.files_from_sizes(sizes, 32)
+    b = hgb.Batch(hg, off)
+    d = to_device(data)
+    o1 = b.cdc_hash(d, hgb.SHA1)
+    o2 = b.outputs(hgb.SHA1)
+    for _ in range(3):                                   # capture once, replay
+        b.cdc_hash(d, hgb.SHA1, out=o2, graph=True)
+    b.sync()
+    assert torch.equal(o1[1], o2[1])
+    for f in range(len(sizes)):
+        a, k = int(b.slot_off[f]), int(o1[1][f])
+        assert torch.equal(o1[0][a:a + k], o2[0][a:a + k])
+        assert torch.equal(o1[2][a:a + k], o2[2][a:a + k])
+    b.close()
+
+
+def test_batch_dense_candidates(hg):
+    """More candidates than the list holds: per-file selection scans the bitmap."""
+    import paper_1202_3669_b300 as hgb
+    p = hgb.params(mask_bits=2, magic=1, min_chunk=64, max_chunk=4096)
+    sizes = [70_000, 1_200_000, 5, 300, 90_000]
+    check_batch(hg, sizes, seed=41, algo=oracle.MD5, p=p)
+
+
+def test_batch_other_params(hg):
+    import paper_1202_3669_b300 as hgb
+    p = hgb.params(window=17, mask_bits=9, magic=0x55, min_chunk=700, max_chunk=5000)
+    sizes = G.lognormal_sizes(40, seed=51, median=30_000, sigma=1.0, hi=2 << 20)
+    check_batch(hg, sizes, seed=52, algo=oracle.SHA1, p=p)
+
+
+def test_batch_autotune_keeps_results(hg):
+    import paper_1202_3669_b300 as hgb
+    sizes = G.lognormal_sizes(200, seed=61, median=64 * 1024, sigma=1.5, hi=8 << 20)
+    data, off = G.files_from_sizes(sizes, 62)
+    b = hgb.Batch(hg, off)
+    d = to_device(data)
+    o1 = b.cdc_hash(d, hgb.SHA1)
+    best = b.autotune(d, hgb.SHA1)
+    assert best.hash_threads in (64, 128, 256) and best.window_ctas_per_sm >= 1
+    o2 = b.cdc_hash(d, hgb.SHA1)
+    b.sync()
+    assert torch.equal(o1[1], o2[1])
+    b.close()
+
+
+def test_config_batch_4096_files(hg):
+    """4096 log-normal files (median 64 KiB, sigma 2.4, 512 B..256 MiB, ~3.6 GiB):
+    every file's chunk count is checked by the rule's own bounds and a sample of
+    files (all sizes up to 4 MiB, plus the largest below 64 MiB) against the oracle."""
+    import paper_1202_3669_b300 as hgb
+    seed, sizes = G.batch_workload_seed()
+    g = G.rng(99)
+    small = np.flatnonzero(sizes <= (4 << 20))
+    sample = sorted(set(g.choice(small, 40, replace=False).tolist()) |
+                    {int(np.flatnonzero(sizes == sizes[sizes < (64 << 20)].max())[0])})
+    out = check_batch(hg, sizes, seed=seed + 1000, algo=oracle.SHA1, graph=True, sample=sample)
+    counts = out[1].cpu().numpy()
+    assert (counts >= np.ceil(sizes / 65536)).all()
+    assert (counts <= sizes // 2048 + 1).all()
