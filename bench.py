@@ -361,6 +361,7 @@ def main():
     if not args.no_extras and rank == 0:
         extras["direct"] = direct_leg(hgb, ctxs[0], dev, flush)
         extras["batch"] = batch_leg(hgb, ctxs[0], dev, flush)
+        extras["serve"] = serve_leg(hgb, ctxs[0], extras["batch"]["batched_graph_GBps"])
         extras["cpu_baseline"] = cpu_baseline(versions)
 
     # max over ranks
@@ -389,7 +390,7 @@ def main():
                "cpu_baseline": extras.get("cpu_baseline"),
                "clocks": clocks,
                "step_ms_p50": statistics.median(step_ms), "step_ms_max": max(step_ms)}
-        for k in ("direct", "batch"):
+        for k in ("direct", "batch", "serve"):
             if k in extras:
                 out[k] = extras[k]
         print(json.dumps(out), flush=True)
@@ -488,6 +489,54 @@ def batch_leg(hgb, ctx, dev, flush):
                        "hash_threads": best.hash_threads, "hash_ctas_per_sm": best.hash_ctas_per_sm,
                        "long_chunk_bytes": best.long_chunk_bytes},
             "note": "per-file: hg_cdc_boundaries + hg_hash_chunks per file on one stream"}
+
+
+def serve_leg(hgb, ctx, capacity_gbps, fracs=(0.1, 0.4, 0.7, 1.0, 1.2), max_req=20000,
+              seconds=2.5):
+    """Open-loop Poisson arrivals at fractions of the batched capacity; request sizes log-normal
+    as in the batch workload; 70 % chunking + MD5, 30 % 64 KiB-block SHA-1 with root; 32 GiB
+    device budget. Payloads come from a 1 GiB pinned pool (request i reads a seeded slice);
+    latency is completion minus scheduled arrival."""
+    import torch
+    from gen import inputs as G
+    pool_bytes = 1 << 30
+    pool = torch.from_numpy(G.uniform_bytes(pool_bytes, seed=77)).pin_memory()
+    base = pool.data_ptr()
+    sctx = hgb.Context(ctx.device.index, budget=40 << 30)      # the server's own context
+    srv = hgb.Server(sctx, device_budget=32 << 30, max_wave_bytes=1 << 30)
+    out = {"capacity_GBps": capacity_gbps, "budget_bytes": 32 << 30, "rates": []}
+    sizes_all = G.lognormal_sizes(200000, seed=78)
+    mean_size = float(sizes_all.mean())
+    for k, frac in enumerate(fracs):
+        lam = frac * capacity_gbps * 1e9 / mean_size
+        n = int(min(max_req, max(200, lam * seconds)))
+        g = G.rng(80 + k)
+        sizes = G.lognormal_sizes(n, seed=90 + k)
+        offs = (g.random(n) * (pool_bytes - sizes)).astype(np.int64)
+        kinds = g.random(n) < 0.7
+        reqs = []
+        for i in range(n):
+            r = hgb.hg_request()
+            r.h_data = base + int(offs[i])
+            r.n = int(sizes[i])
+            if kinds[i]:
+                r.kind, r.algo, r.block, r.want_root = hgb.HG_REQ_CDC, hgb.MD5, 0, 0
+            else:
+                r.kind, r.algo, r.block, r.want_root = hgb.HG_REQ_BLOCKS, hgb.SHA1, 65536, 1
+            reqs.append(r)
+        arrivals = (G.poisson_arrivals(lam, n, seed=100 + k) * 1e9).astype(np.uint64)
+        lat, span = srv.replay(reqs, arrivals)
+        lat_ms = lat.astype(np.float64) / 1e6
+        total = int(sizes.sum())
+        out["rates"].append({"frac": frac, "requests": n, "offered_GBps": total / (arrivals[-1] / 1e9) / 1e9,
+                             "achieved_GBps": total / (span / 1e9) / 1e9,
+                             "p50_ms": float(np.percentile(lat_ms, 50)),
+                             "p99_ms": float(np.percentile(lat_ms, 99)),
+                             "mean_request_bytes": total / n})
+    out["waves"] = srv.stats()["waves"]
+    srv.close()
+    sctx.close()
+    return out
 
 
 if __name__ == "__main__":

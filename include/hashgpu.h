@@ -210,6 +210,87 @@ int hg_batch_autotune(hg_batch *batch, int algo, const uint8_t *d_data, uint64_t
                       uint64_t *d_counts, uint8_t *d_digests, void *stream, hg_batch_tuning *best);
 
 /*
+ * Request server with continuous batching (Sec. 3.2.3: applications submit
+ * jobs to an outstanding queue, a manager thread per GPU runs them and
+ * notifies completion; buffers are preallocated and reused; transfers overlap
+ * computation). One progress thread per server admits requests in arrival
+ * order while their input fits in a device arena of device_budget bytes
+ * (allocated once at creation, with the per-wave scratch carved from the same
+ * budget), copies them to the device on a copy stream, and runs everything
+ * admitted together as one wave: one batched chunking job for the chunking
+ * requests and the fixed-block kernels for the block requests, then one copy
+ * of the wave's outputs to pinned host memory. Up to max_inflight_waves waves
+ * are on the GPU at once; requests that arrive meanwhile are admitted as soon
+ * as arena memory and a wave slot free up.
+ *
+ * Results are exactly those of hg_cdc_boundaries + hg_hash_chunks (kind
+ * HG_REQ_CDC, chunking with the server's cdc parameters) or hg_hash_blocks
+ * (kind HG_REQ_BLOCKS) on the request alone.
+ */
+typedef enum { HG_REQ_CDC = 0, HG_REQ_BLOCKS = 1 } hg_req_kind;
+
+typedef struct {
+    int32_t kind;            /* hg_req_kind */
+    int32_t algo;            /* HG_MD5 / HG_SHA1 */
+    const uint8_t *h_data;   /* host bytes; pinned memory gives one-copy DMA (Sec. 3.1) */
+    uint64_t n;              /* bytes */
+    uint64_t block;          /* HG_REQ_BLOCKS: block size */
+    int32_t want_root;       /* HG_REQ_BLOCKS: also the hash-of-hashes */
+    int32_t reserved;
+} hg_request;
+
+typedef struct {
+    int32_t status;          /* HG_OK or HG_ECANCELED */
+    int32_t algo;
+    uint64_t count;          /* chunks or blocks */
+    const uint64_t *ends;    /* HG_REQ_CDC: chunk ends (count), NULL otherwise */
+    const uint8_t *digests;  /* count * dlen bytes */
+    uint8_t root[20];        /* HG_REQ_BLOCKS with want_root */
+    uint64_t t_submit_ns, t_admit_ns, t_done_ns;   /* steady-clock timestamps */
+} hg_result;
+
+typedef struct {
+    uint64_t device_budget;       /* device bytes for staging + wave scratch (32 GiB) */
+    uint64_t max_wave_bytes;      /* input bytes per wave; larger requests are refused (1 GiB) */
+    uint32_t max_wave_requests;   /* requests per wave (4096) */
+    uint32_t max_inflight_waves;  /* waves on the GPU at once, 1..8 (2) */
+    hg_cdc_params cdc;            /* chunking parameters of HG_REQ_CDC requests */
+} hg_server_config;
+
+typedef struct {
+    uint64_t submitted, completed, cancelled, waves, bytes_done;
+    uint64_t arena_used, arena_bytes, queued;
+} hg_server_stats;
+
+typedef struct hg_server hg_server;
+
+void hg_server_default_config(hg_server_config *cfg);
+/* HG_ENOMEM when the budget cannot hold the wave scratch plus one maximal wave
+ * or exceeds the context's budget. Starts the progress thread. */
+int hg_server_create(hg_ctx *ctx, const hg_server_config *cfg, hg_server **out);
+/* Cancels requests not yet admitted, waits for the waves on the GPU, frees everything. */
+int hg_server_destroy(hg_server *srv);
+/* Queue a request; returns at once with a ticket. HG_ENOMEM if the request
+ * alone exceeds a wave or the arena (it could never be admitted). The host
+ * bytes must stay valid and unchanged until the request completes. */
+int hg_submit(hg_server *srv, const hg_request *req, uint64_t *ticket);
+/* Cancel a request that is still queued (HG_EAGAIN once admitted). */
+int hg_cancel(hg_server *srv, uint64_t ticket);
+/* Wait up to timeout_us (-1: forever, 0: do not wait) for a request; HG_EAGAIN
+ * if not done. The result's arrays stay valid until hg_release. */
+int hg_poll(hg_server *srv, uint64_t ticket, hg_result *res, int64_t timeout_us);
+int hg_release(hg_server *srv, uint64_t ticket);
+/* Tickets completed since the previous call (up to max), waiting up to timeout_us for one. */
+int hg_server_wait_any(hg_server *srv, uint64_t *tickets, uint32_t max, int64_t timeout_us,
+                       uint32_t *n_out);
+int hg_server_get_stats(hg_server *srv, hg_server_stats *stats);
+/* Replay an open-loop trace: request i is submitted at arrival_ns[i] after the
+ * call starts (non-decreasing); latency_ns[i] receives its completion time
+ * minus its scheduled arrival; *span_ns the whole replay's duration. */
+int hg_server_replay(hg_server *srv, const hg_request *reqs, const uint64_t *arrival_ns,
+                     uint32_t nreq, uint64_t *latency_ns, uint64_t *span_ns);
+
+/*
  * Chunk boundaries without allocating: the same result as hg_cdc_boundaries,
  * for callers that cannot call cudaMalloc -- a write path that must not stall
  * on the device-wide synchronisation cudaMalloc/cudaFree can cause, a process

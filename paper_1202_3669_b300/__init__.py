@@ -6,6 +6,8 @@ raw C functions are re-exported under their C names from `_lib`.
 """
 from __future__ import annotations
 
+import ctypes as C
+
 import numpy as np
 import torch
 
@@ -15,7 +17,11 @@ from ._lib import (HG_MD5, HG_SHA1, HashGPUError, check, default_params,  # noqa
                    hg_batch_destroy, hg_batch_get_tuning, hg_batch_set_tuning, hg_batch_slots,
                    hg_batch_sync, hg_batch_tuning, hg_cdc_boundaries, hg_cdc_boundaries_static,
                    hg_cdc_candidates, hg_cdc_params, hg_destroy, hg_digest_len, hg_hash_blocks,
-                   hg_hash_chunks, hg_init, hg_reserve, hg_scratch_bytes, hg_sync, hg_window_bitmap)
+                   hg_hash_chunks, hg_init, hg_reserve, hg_scratch_bytes, hg_sync, hg_window_bitmap,
+                   HG_REQ_BLOCKS, HG_REQ_CDC, hg_cancel, hg_poll, hg_release, hg_request, hg_result,
+                   hg_server_config, hg_server_create, hg_server_default_config, hg_server_destroy,
+                   hg_server_get_stats, hg_server_replay, hg_server_stats, hg_server_wait_any,
+                   hg_submit)
 
 MD5, SHA1 = HG_MD5, HG_SHA1
 DIGEST_LEN = {MD5: 16, SHA1: 20}
@@ -201,3 +207,111 @@ class Batch:
         k = int(counts[f].item())
         a = int(self.slot_off[f])
         return (ends[a:a + k].cpu().numpy().astype(np.uint64), dg[a:a + k].cpu().numpy())
+
+
+class Server:
+    """Request server with continuous batching (one progress thread per server).
+
+    Requests reference host memory (numpy arrays or pinned torch tensors) that
+    must stay alive until the request completes; `submit` keeps a reference.
+    """
+
+    def __init__(self, ctx: Context, device_budget: int | None = None,
+                 max_wave_bytes: int | None = None, max_wave_requests: int | None = None,
+                 max_inflight_waves: int | None = None, p: hg_cdc_params | None = None):
+        cfg = hg_server_config()
+        hg_server_default_config(cfg)
+        if device_budget is not None:
+            cfg.device_budget = device_budget
+        if max_wave_bytes is not None:
+            cfg.max_wave_bytes = max_wave_bytes
+        if max_wave_requests is not None:
+            cfg.max_wave_requests = max_wave_requests
+        if max_inflight_waves is not None:
+            cfg.max_inflight_waves = max_inflight_waves
+        if p is not None:
+            cfg.cdc = p
+        self.cfg = cfg
+        self.ctx = ctx
+        self.h = hg_server_create(ctx.h, cfg)
+        self._keep: dict[int, object] = {}
+
+    @staticmethod
+    def _host_ptr(data):
+        if isinstance(data, torch.Tensor):
+            return data.data_ptr() if data.numel() else None, data.numel()
+        a = np.ascontiguousarray(data)
+        return (a.ctypes.data if a.size else None), a.size
+
+    def make_request(self, data, kind: int = HG_REQ_CDC, algo: int = MD5, block: int = 0,
+                     want_root: bool = False) -> hg_request:
+        ptr, n = self._host_ptr(data)
+        r = hg_request()
+        r.kind, r.algo, r.h_data, r.n, r.block, r.want_root, r.reserved = \
+            kind, algo, ptr, n, block, int(want_root), 0
+        return r
+
+    def submit(self, data, kind: int = HG_REQ_CDC, algo: int = MD5, block: int = 0,
+               want_root: bool = False) -> int:
+        r = self.make_request(data, kind, algo, block, want_root)
+        rc, t = hg_submit(self.h, r)
+        check(rc, "hg_submit")
+        self._keep[t] = data
+        return t
+
+    def cancel(self, ticket: int) -> int:
+        return hg_cancel(self.h, ticket)
+
+    def poll(self, ticket: int, timeout_us: int = -1, release: bool = True):
+        """dict of the result, or None if not done within timeout_us."""
+        res = hg_result()
+        rc = hg_poll(self.h, ticket, res, timeout_us)
+        if rc == _lib.HG_EAGAIN:
+            return None
+        check(rc, "hg_poll")
+        dl = DIGEST_LEN[res.algo]
+        k = res.count
+        out = {"status": res.status, "count": k,
+               "ends": np.ctypeslib.as_array(res.ends, (k,)).copy() if res.ends else None,
+               "digests": (np.ctypeslib.as_array(res.digests, (k * dl,)).reshape(k, dl).copy()
+                           if res.digests else np.zeros((0, dl), np.uint8)),
+               "root": bytes(res.root[:dl]),
+               "t_submit_ns": res.t_submit_ns, "t_admit_ns": res.t_admit_ns,
+               "t_done_ns": res.t_done_ns}
+        if release:
+            hg_release(self.h, ticket)
+            self._keep.pop(ticket, None)
+        return out
+
+    def wait_any(self, max_n: int = 1024, timeout_us: int = -1) -> list[int]:
+        buf = np.zeros(max_n, np.uint64)
+        rc, n = hg_server_wait_any(self.h, buf.ctypes.data, max_n, timeout_us)
+        check(rc, "hg_server_wait_any")
+        return buf[:n].tolist()
+
+    def stats(self) -> dict:
+        st = hg_server_stats()
+        check(hg_server_get_stats(self.h, st))
+        return {k: getattr(st, k) for k, _ in st._fields_}
+
+    def replay(self, reqs: list, arrivals_ns: np.ndarray):
+        """Open-loop replay of (request, arrival) pairs; returns (latencies_ns, span_ns)."""
+        arr = (hg_request * len(reqs))(*reqs)
+        t = np.ascontiguousarray(arrivals_ns, dtype=np.uint64)
+        lat = np.zeros(len(reqs), np.uint64)
+        rc, span = hg_server_replay(self.h, C.cast(arr, C.c_void_p).value, t.ctypes.data,
+                                    len(reqs), lat.ctypes.data)
+        check(rc, "hg_server_replay")
+        return lat, span
+
+    def close(self):
+        if getattr(self, "h", None):
+            hg_server_destroy(self.h)
+            self.h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -31,6 +31,33 @@ class hg_cdc_params(C.Structure):
                 ("reserved", C.c_uint32), ("min_chunk", C.c_uint64), ("max_chunk", C.c_uint64)]
 
 
+HG_REQ_CDC, HG_REQ_BLOCKS = 0, 1
+
+
+class hg_request(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("algo", C.c_int32), ("h_data", C.c_void_p),
+                ("n", C.c_uint64), ("block", C.c_uint64), ("want_root", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class hg_result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("algo", C.c_int32), ("count", C.c_uint64),
+                ("ends", C.POINTER(C.c_uint64)), ("digests", C.POINTER(C.c_uint8)),
+                ("root", C.c_uint8 * 20), ("t_submit_ns", C.c_uint64),
+                ("t_admit_ns", C.c_uint64), ("t_done_ns", C.c_uint64)]
+
+
+class hg_server_config(C.Structure):
+    _fields_ = [("device_budget", C.c_uint64), ("max_wave_bytes", C.c_uint64),
+                ("max_wave_requests", C.c_uint32), ("max_inflight_waves", C.c_uint32),
+                ("cdc", hg_cdc_params)]
+
+
+class hg_server_stats(C.Structure):
+    _fields_ = [(k, C.c_uint64) for k in ("submitted", "completed", "cancelled", "waves",
+                                          "bytes_done", "arena_used", "arena_bytes", "queued")]
+
+
 SIGNATURES = {
     "hg_cdc_default_params": (None, [C.POINTER(hg_cdc_params)]),
     "hg_strerror": (C.c_char_p, [_i32]),
@@ -54,6 +81,16 @@ SIGNATURES = {
     "hg_batch_get_tuning": (_i32, [_vp, _vp]),
     "hg_batch_set_tuning": (_i32, [_vp, _vp]),
     "hg_batch_autotune": (_i32, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "hg_server_default_config": (None, [C.POINTER(hg_server_config)]),
+    "hg_server_create": (_i32, [_vp, C.POINTER(hg_server_config), C.POINTER(_vp)]),
+    "hg_server_destroy": (_i32, [_vp]),
+    "hg_submit": (_i32, [_vp, C.POINTER(hg_request), C.POINTER(C.c_uint64)]),
+    "hg_cancel": (_i32, [_vp, _u64]),
+    "hg_poll": (_i32, [_vp, _u64, C.POINTER(hg_result), C.c_int64]),
+    "hg_release": (_i32, [_vp, _u64]),
+    "hg_server_wait_any": (_i32, [_vp, _vp, _u32, C.c_int64, C.POINTER(C.c_uint32)]),
+    "hg_server_get_stats": (_i32, [_vp, C.POINTER(hg_server_stats)]),
+    "hg_server_replay": (_i32, [_vp, _vp, _vp, _u32, _vp, C.POINTER(C.c_uint64)]),
     "hg_cdc_boundaries_static": (_i32, [_vp, _u64, C.POINTER(hg_cdc_params), _vp, _u64, _vp, _vp]),
 }
 
@@ -182,3 +219,51 @@ def hg_batch_set_tuning(batch, tuning) -> int:
 def hg_batch_autotune(batch, algo, d_data, d_ends, d_counts, d_digests, stream, best) -> int:
     return lib.hg_batch_autotune(batch, algo, d_data, d_ends, d_counts, d_digests, stream,
                                  C.byref(best) if best is not None else None)
+
+
+def hg_server_default_config(cfg) -> None:
+    lib.hg_server_default_config(C.byref(cfg))
+
+
+def hg_server_create(ctx, cfg) -> int:
+    h = _vp()
+    check(lib.hg_server_create(ctx, C.byref(cfg), C.byref(h)), "hg_server_create")
+    return h.value
+
+
+def hg_server_destroy(srv) -> int:
+    return lib.hg_server_destroy(srv)
+
+
+def hg_submit(srv, req) -> tuple[int, int]:
+    t = C.c_uint64()
+    rc = lib.hg_submit(srv, C.byref(req), C.byref(t))
+    return rc, t.value
+
+
+def hg_cancel(srv, ticket) -> int:
+    return lib.hg_cancel(srv, ticket)
+
+
+def hg_poll(srv, ticket, res, timeout_us) -> int:
+    return lib.hg_poll(srv, ticket, C.byref(res), timeout_us)
+
+
+def hg_release(srv, ticket) -> int:
+    return lib.hg_release(srv, ticket)
+
+
+def hg_server_wait_any(srv, tickets_ptr, max_n, timeout_us) -> tuple[int, int]:
+    n = C.c_uint32()
+    rc = lib.hg_server_wait_any(srv, tickets_ptr, max_n, timeout_us, C.byref(n))
+    return rc, n.value
+
+
+def hg_server_get_stats(srv, st) -> int:
+    return lib.hg_server_get_stats(srv, C.byref(st))
+
+
+def hg_server_replay(srv, reqs_ptr, arrivals_ptr, nreq, lat_ptr) -> tuple[int, int]:
+    span = C.c_uint64()
+    rc = lib.hg_server_replay(srv, reqs_ptr, arrivals_ptr, nreq, lat_ptr, C.byref(span))
+    return rc, span.value

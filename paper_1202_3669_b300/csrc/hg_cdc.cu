@@ -263,6 +263,13 @@ int launch_compact(const uint32_t *d_bitmap, uint64_t n, const uint32_t *d_tile_
     return cuda_status(cudaGetLastError());
 }
 
+int launch_scan_tiles(const uint32_t *d_tile_cnt, uint64_t ntiles, uint64_t *d_tile_off,
+                      uint64_t *d_total, cudaStream_t s) {
+    if (ntiles == 0) return cuda_status(cudaMemsetAsync(d_total, 0, sizeof(uint64_t), s));
+    k_scan_tiles<<<1, 1024, 0, s>>>(d_tile_cnt, ntiles, d_tile_off, d_total);
+    return cuda_status(cudaGetLastError());
+}
+
 int launch_select(const uint64_t *d_cands, const uint64_t *d_ncand, uint64_t cand_cap,
                   const uint32_t *d_bitmap, uint64_t n, const hg_cdc_params &p, uint64_t *d_ends,
                   uint64_t cap, uint64_t *d_count, cudaStream_t s) {

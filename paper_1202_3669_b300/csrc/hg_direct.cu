@@ -54,7 +54,59 @@ __global__ void __launch_bounds__(128) k_hash_chunks(const uint8_t *__restrict__
     store_digest(hs, out + i * H::kDigest);
 }
 
+// All fixed-block requests of a batch in one launch: one thread per block of
+// any request (block i of request r is global block reqs[r].first + i).
+__global__ void __launch_bounds__(128) k_multi_blocks(const BlkReq *__restrict__ reqs, uint32_t nreq,
+                                                      uint64_t total_blocks) {
+    const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= total_blocks) return;
+    uint32_t lo = 0, hi = nreq;                       // last r with first <= g
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) / 2;
+        if (reqs[mid].first <= g) lo = mid; else hi = mid;
+    }
+    const BlkReq r = reqs[lo];
+    const uint64_t i = g - r.first;
+    const uint64_t off = i * r.block;
+    const uint64_t len = (r.len - off < r.block) ? r.len - off : r.block;
+    if (r.algo == HG_MD5) {
+        Md5 hs;
+        hash_range(r.ptr + off, len, hs);
+        store_digest(hs, r.out + i * Md5::kDigest);
+    } else {
+        Sha1 hs;
+        hash_range(r.ptr + off, len, hs);
+        store_digest(hs, r.out + i * Sha1::kDigest);
+    }
+}
+
+// Hash-of-hashes of every request that asks for one (one thread each); its
+// root goes right after its block digests.
+__global__ void k_multi_roots(const BlkReq *__restrict__ reqs, uint32_t nreq) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nreq || !reqs[k].root) return;
+    const BlkReq r = reqs[k];
+    const uint64_t nblk = (r.len + r.block - 1) / r.block;
+    if (r.algo == HG_MD5) {
+        Md5 hs;
+        hash_range(r.out, nblk * Md5::kDigest, hs);
+        store_digest(hs, r.out + nblk * Md5::kDigest);
+    } else {
+        Sha1 hs;
+        hash_range(r.out, nblk * Sha1::kDigest, hs);
+        store_digest(hs, r.out + nblk * Sha1::kDigest);
+    }
+}
+
 }  // namespace
+
+int launch_multi_blocks(const BlkReq *d_reqs, uint32_t nreq, uint64_t total_blocks, cudaStream_t s) {
+    if (nreq == 0) return HG_OK;
+    if (total_blocks)
+        k_multi_blocks<<<(unsigned)((total_blocks + 127) / 128), 128, 0, s>>>(d_reqs, nreq, total_blocks);
+    k_multi_roots<<<(nreq + 127) / 128, 128, 0, s>>>(d_reqs, nreq);
+    return cuda_status(cudaGetLastError());
+}
 
 int launch_hash_blocks(int algo, const uint8_t *d_in, uint64_t n, uint64_t block,
                        uint8_t *d_digests, cudaStream_t s, int *) {

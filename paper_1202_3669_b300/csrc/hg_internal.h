@@ -2,6 +2,7 @@
 #pragma once
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "hashgpu.h"
@@ -45,16 +46,84 @@ int launch_hash_chunks(int algo, const uint8_t *d_in, uint64_t n, const uint64_t
                        uint64_t nchunk,
                        const uint64_t *d_count, uint8_t *d_digests, cudaStream_t s, int *d_err);
 
+// Fixed-block request of a batched launch: blocks of `block` bytes of ptr[0..len),
+// digests to out (4-byte aligned), root (if asked) right after them.
+struct BlkReq {
+    const uint8_t *ptr;
+    uint64_t len, block;
+    uint64_t first;        // global index of its first block in the launch
+    uint8_t *out;
+    int32_t algo, root;
+};
+int launch_multi_blocks(const BlkReq *d_reqs, uint32_t nreq, uint64_t total_blocks, cudaStream_t s);
+
 // hg_cdc.cu
 int launch_window_bitmap(const uint8_t *d_in, uint64_t n, const hg_cdc_params &p,
                          uint32_t *d_bitmap, uint32_t *d_tile_cnt, cudaStream_t s, int *d_err);
 int launch_compact(const uint32_t *d_bitmap, uint64_t n, const uint32_t *d_tile_cnt,
                    uint64_t *d_tile_off, uint64_t ntiles, uint64_t *d_cands, uint64_t cap,
                    uint64_t *d_count, cudaStream_t s);
+int launch_scan_tiles(const uint32_t *d_tile_cnt, uint64_t ntiles, uint64_t *d_tile_off,
+                      uint64_t *d_total, cudaStream_t s);
 int launch_select(const uint64_t *d_cands, const uint64_t *d_ncand, uint64_t cand_cap,
                   const uint32_t *d_bitmap, uint64_t n, const hg_cdc_params &p, uint64_t *d_ends,
                   uint64_t cap, uint64_t *d_count, cudaStream_t s);
 
 inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? HG_OK : HG_ECUDA; }
+
+// ---- batched chunking jobs (hg_job.cu) -------------------------------------------------
+// Files from this size up select their boundaries with a whole CTA.
+constexpr uint64_t kJobBigFileBytes = 1ull << 20;
+// counters of a job (device words)
+enum { kJobTotal = 0, kJobFront = 1, kJobBack = 2, kJobTaskCtr = 3, kJobTileCtr = 4, kJobNumWords = 8 };
+
+// Device view of a job: file f is jptr(f) .. + jlen(f): base + file_off[f] when
+// base is set (files back to back), else file_ptr[f] / file_len[f]. Its tiles
+// are [tile_start[f], tile_start[f+1]), its output slots [slot_off[f],
+// slot_off[f+1]); small / big list the files by selection method.
+struct JobDev {
+    const uint8_t *base;
+    const uint64_t *file_off;
+    const uint8_t *const *file_ptr;
+    const uint64_t *file_len;
+    const uint64_t *tile_start;
+    const uint64_t *slot_off;
+    const uint32_t *small;
+    const uint32_t *big;
+    uint32_t nfile, nsmall, nbig, ntiles;
+};
+
+struct JobScratch {
+    uint32_t *bitmap;      // ntiles * kWinThreads words
+    uint32_t *tile_cnt;    // ntiles
+    uint64_t *tile_off;    // ntiles + 1 (last = candidate count)
+    uint64_t *cands;
+    uint64_t cand_cap;
+    uint64_t *tasks;       // total_slots
+    unsigned long long *words;
+    int *err;
+};
+
+struct JobTuning {
+    int window_ctas;       // persistent window CTAs per SM
+    int hash_threads;
+    int hash_ctas;         // chunk-hash CTAs per SM
+    uint64_t long_bytes;   // chunks at least this long are hashed first
+};
+
+struct JobHost {
+    std::vector<uint64_t> tile_start, slot_off;
+    std::vector<uint32_t> small, big;
+    uint64_t ntiles = 0, total_slots = 0;
+};
+
+void job_plan(const uint64_t *len, uint32_t nfile, uint64_t min_chunk, JobHost *h);
+size_t job_scratch_bytes(uint64_t ntiles, uint64_t cand_cap, uint64_t total_slots);
+void job_scratch_carve(char *mem, uint64_t ntiles, uint64_t cand_cap, uint64_t total_slots,
+                       JobScratch *sc);
+int job_window_occupancy(uint32_t window);
+int enqueue_cdc_job(const JobDev &j, const JobScratch &sc, const hg_cdc_params &p, int algo,
+                    const JobTuning &tn, int num_sms, uint64_t *d_ends, uint64_t *d_counts,
+                    uint8_t *d_digests, cudaStream_t s);
 
 }  // namespace hg
