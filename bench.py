@@ -40,10 +40,18 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 METRIC = "hashed GB/s (CDC: 20-byte MD5 window + min/max boundaries + per-chunk MD5)"
+# hg_cdc_hash is the public call timed; hg_cdc_boundaries + hg_hash_chunks (the
+# same kernels without segment pipelining) is reported beside it.
 UNIT = "GB/s"
 WORKLOAD = "cdc_64MiB_base_plus_1pct_edited_version"
-OPS_PER_WINDOW = 270          # algorithmic 32-bit integer ops per window hash
-INT_LANES_PER_SM_CLK = 128    # 4 schedulers x 32 lanes issue per SM per clock
+# Algorithmic cost of one window hash in integer-ALU instructions (3-input logic op,
+# 3-input add and the rotate-add each count one): 42 operations with a constant
+# message word x 3 + 19 with a data word x 4, + 3.75 funnel shifts to assemble
+# the window, + 4 for the test and bit collection = 208 (derivation in the design doc).
+ALU_OPS_PER_WINDOW = 208
+ALU_LANES_PER_SM_CLK = 64     # integer ALU pipe: one warp instruction per 2 clocks per scheduler
+SURVEY_OPS_PER_WINDOW = 270   # the same work counted in 2-input operations
+ISSUE_LANES_PER_SM_CLK = 128  # 4 schedulers x 32 lanes
 WINDOW_KERNEL_SRC = os.path.join(ROOT, "paper_1202_3669_b300", "csrc", "hg_cdc.cu")
 
 
@@ -53,7 +61,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-extras", action="store_true", help="skip direct-hash and CPU legs")
+    ap.add_argument("--no-extras", action="store_true", help="skip the direct/batch/serve/CPU legs")
+    ap.add_argument("--leg", default=None, choices=["direct", "batch", "serve"],
+                    help="run only this extra leg (for profiling) and print its result")
     return ap.parse_args()
 
 
@@ -214,6 +224,17 @@ def main():
         if world > 1:
             dist.barrier()
 
+    if args.leg:
+        ctx = hgb.Context(local)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+        if args.leg == "direct":
+            res = direct_leg(hgb, ctx, dev, flush)
+        elif args.leg == "batch":
+            res = batch_leg(hgb, ctx, dev, flush)
+        else:
+            res = serve_leg(hgb, ctx, batch_leg(hgb, ctx, dev, flush)["batched_graph_GBps"])
+        print(json.dumps({"leg": args.leg, "result": res}), flush=True)
+        return
     versions = workload()
     nbytes = sum(v.size for v in versions)
     p = hgb.default_params()
@@ -235,12 +256,12 @@ def main():
         for i in range(len(versions)):
             s = streams[i]
             s.wait_event(ev0)
-            ctxs[i].cdc_boundaries(src[i], p, cap=cap[i], out=ends[i], count=cnts[i], stream=s)
-            ctxs[i].hash_chunks(src[i], ends[i], hgb.MD5, count=cnts[i], out=dgs[i], stream=s)
+            ctxs[i].cdc_hash(src[i], hgb.MD5, p, out=(ends[i], cnts[i], dgs[i]), stream=s)
         for s in streams:
             main_s.wait_stream(s)
 
-    launches_per_step = 5 * len(versions)    # window, scan, compact, select, chunk hash
+    # hg_cdc_hash: five kernels per segment (window, scan, compact, select, chunk digests)
+    launches_per_step = sum(5 * (len(hgb.cdc_hash_plan(v.size)) - 1) for v in versions)
     for _ in range(args.warmup):
         step(d_in)
     torch.cuda.synchronize()
@@ -269,6 +290,30 @@ def main():
     step_ms = [a.elapsed_time(b) for a, b in ms]
     t_dev = sum(step_ms) / len(step_ms)
 
+    # the same work through the two unpipelined calls, for comparison
+    def step_two_calls(src):
+        ev0 = torch.cuda.Event()
+        ev0.record(main_s)
+        for i in range(len(versions)):
+            s = streams[i]
+            s.wait_event(ev0)
+            ctxs[i].cdc_boundaries(src[i], p, cap=cap[i], out=ends[i], count=cnts[i], stream=s)
+            ctxs[i].hash_chunks(src[i], ends[i], hgb.MD5, count=cnts[i], out=dgs[i], stream=s)
+        for s in streams:
+            main_s.wait_stream(s)
+
+    step_two_calls(d_in)
+    tw = []
+    for _ in range(20):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(main_s)
+        step_two_calls(d_in)
+        b.record(main_s)
+        tw.append((a, b))
+    torch.cuda.synchronize()
+    t_two = sum(a.elapsed_time(b) for a, b in tw) / len(tw)
+
     # e2e: pinned host inputs -> device -> boundaries + digests -> pinned host
     h_in = [torch.from_numpy(v).pin_memory() for v in versions]
     h_ends = [torch.empty(c, dtype=torch.int64).pin_memory() for c in cap]
@@ -277,6 +322,15 @@ def main():
     d_in2 = [torch.empty_like(x) for x in d_in]
     h2d = sum(v.size for v in versions)
     d2h = sum(e.numel() * 8 + 8 + d.numel() for e, d in zip(h_ends, h_dg))
+    # plain pinned host -> device copy rate, for context of the e2e figure
+    a, bq = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    d_in2[0].copy_(h_in[0], non_blocking=True)
+    a.record(main_s)
+    for _ in range(5):
+        d_in2[0].copy_(h_in[0], non_blocking=True)
+    bq.record(main_s)
+    torch.cuda.synchronize()
+    h2d_gbps = 5 * versions[0].size / (a.elapsed_time(bq) / 1e3) / 1e9
 
     def e2e_step():
         ev0 = torch.cuda.Event()
@@ -286,8 +340,7 @@ def main():
             s.wait_event(ev0)
             with torch.cuda.stream(s):
                 d_in2[i].copy_(h_in[i], non_blocking=True)
-            ctxs[i].cdc_boundaries(d_in2[i], p, cap=cap[i], out=ends[i], count=cnts[i], stream=s)
-            ctxs[i].hash_chunks(d_in2[i], ends[i], hgb.MD5, count=cnts[i], out=dgs[i], stream=s)
+            ctxs[i].cdc_hash(d_in2[i], hgb.MD5, p, out=(ends[i], cnts[i], dgs[i]), stream=s)
             with torch.cuda.stream(s):
                 h_cnt[i].copy_(cnts[i], non_blocking=True)
                 h_ends[i].copy_(ends[i], non_blocking=True)
@@ -337,15 +390,18 @@ def main():
     peaks, peak_kind = measured_peaks()
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_max = float(peaks.get("sm_max_mhz", 2032.0))
-    peak_tops = sm_count * INT_LANES_PER_SM_CLK * sm_max * 1e6 / 1e12
-    achieved = windows * OPS_PER_WINDOW / t_win / 1e12
+    peak_tops = sm_count * ALU_LANES_PER_SM_CLK * sm_max * 1e6 / 1e12
+    achieved = windows * ALU_OPS_PER_WINDOW / t_win / 1e12
+    issue_peak = sm_count * ISSUE_LANES_PER_SM_CLK * sm_max * 1e6 / 1e12
     tr = kernel_traffic("k_window_bitmap", WINDOW_KERNEL_SRC)
     roofline = {"bound": "alu", "kernel": "k_window_bitmap<20>", "achieved": achieved,
-                "peak": peak_tops, "unit": "Tops/s (int32)", "frac": achieved / peak_tops,
-                "peak_kind": f"{sm_count} SMs x {INT_LANES_PER_SM_CLK} int32 lanes/clk x "
-                             f"{sm_max:.0f} MHz (max SM clock, {peak_kind})",
-                "ops_per_window": OPS_PER_WINDOW, "windows_per_launch": windows,
+                "peak": peak_tops, "unit": "Tops/s (int32 ALU-pipe instructions)",
+                "frac": achieved / peak_tops,
+                "peak_kind": f"{sm_count} SMs x {ALU_LANES_PER_SM_CLK} lanes/clk (integer ALU pipe) x "
+                             f"{sm_max:.0f} MHz (max SM clock, {peak_kind} clock); recipe unit counts",
+                "ops_per_window": ALU_OPS_PER_WINDOW, "windows_per_launch": windows,
                 "launch_ms": t_win * 1e3, "window_GBps": versions[0].size / t_win / 1e9,
+                "frac_survey_count_vs_issue_peak": windows * SURVEY_OPS_PER_WINDOW / t_win / 1e12 / issue_peak,
                 "traffic": (tr["dram_bytes_per_launch"] * versions[0].size / tr["input_bytes"]) if tr else None}
     if clocks.get("sm_mhz"):
         roofline["frac_at_observed_clock"] = achieved / (peak_tops * clocks["sm_mhz"] / sm_max)
@@ -384,12 +440,15 @@ def main():
                           "l2": "flushed between steps (256 MiB memset)",
                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                "e2e": {"value": world * nbytes / (t_e2e_all / 1e3) / 1e9, "unit": UNIT,
-                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                       "pinned_h2d_copy_GBps": h2d_gbps},
                "gpu_launches": launches_per_step * args.steps,
                "roofline": roofline,
                "cpu_baseline": extras.get("cpu_baseline"),
                "clocks": clocks,
-               "step_ms_p50": statistics.median(step_ms), "step_ms_max": max(step_ms)}
+               "step_ms_p50": statistics.median(step_ms), "step_ms_max": max(step_ms),
+               "unpipelined": {"GBps": nbytes / (t_two / 1e3) / 1e9, "ms_per_step": t_two,
+                               "calls": "hg_cdc_boundaries + hg_hash_chunks"}}
         for k in ("direct", "batch", "serve"):
             if k in extras:
                 out[k] = extras[k]

@@ -159,6 +159,27 @@ int hg_hash_chunks(hg_ctx *ctx, int algo, const uint8_t *d_in, uint64_t n, const
                    uint64_t nchunk, const uint64_t *d_count, uint8_t *d_digests, void *stream);
 
 /*
+ * Chunk boundaries and per-chunk digests of one buffer in one call: the same
+ * results as hg_cdc_boundaries followed by hg_hash_chunks (Fig. 3: sliding-
+ * window hashing, boundary detection, then direct hashing of each chunk). The
+ * launches are captured once into a CUDA graph (per context, replayed while
+ * the arguments stay the same). Buffers above 64 MiB are processed in
+ * segments of at least 32 MiB: every chunk is digested as soon as the
+ * candidates seen so far decide its end, while later segments are still being
+ * window-hashed. Runs on context-owned streams forked from and joined back
+ * into `stream`. d_ends needs cap >= n / min_chunk + 1 entries (HG_ECAPACITY
+ * otherwise, before anything is enqueued); d_digests cap * dlen bytes;
+ * *d_count (device) gets the count.
+ */
+int hg_cdc_hash(hg_ctx *ctx, int algo, const uint8_t *d_in, uint64_t n, const hg_cdc_params *params,
+                uint64_t *d_ends, uint64_t cap, uint64_t *d_count, uint8_t *d_digests,
+                void *stream);
+/* The segment schedule hg_cdc_hash uses for n bytes: returns the number of
+ * segments S (0 for n = 0) and writes up to max of the S + 1 bounds (0 ...
+ * n) when bounds is not NULL. Each segment enqueues five kernels. */
+uint32_t hg_cdc_hash_plan(uint64_t n, uint64_t *bounds, uint32_t max);
+
+/*
  * Batched chunking and chunk digests for many files in one pass (Sec. 3.2.3:
  * the runtime batches a stream of hashing jobs; Sec. 4.1: the gains need
  * batches; Sec. 3.2.4: writes are buffered so one GPU job covers many chunks).

@@ -21,7 +21,7 @@ from ._lib import (HG_MD5, HG_SHA1, HashGPUError, check, default_params,  # noqa
                    HG_REQ_BLOCKS, HG_REQ_CDC, hg_cancel, hg_poll, hg_release, hg_request, hg_result,
                    hg_server_config, hg_server_create, hg_server_default_config, hg_server_destroy,
                    hg_server_get_stats, hg_server_replay, hg_server_stats, hg_server_wait_any,
-                   hg_submit)
+                   hg_submit, hg_cdc_hash, hg_cdc_hash_plan)
 
 MD5, SHA1 = HG_MD5, HG_SHA1
 DIGEST_LEN = {MD5: 16, SHA1: 20}
@@ -32,6 +32,14 @@ def params(window=20, mask_bits=13, magic=0x0F0F, min_chunk=2048, max_chunk=6553
     p.window, p.mask_bits, p.magic, p.reserved = window, mask_bits, magic, 0
     p.min_chunk, p.max_chunk = min_chunk, max_chunk
     return p
+
+
+def cdc_hash_plan(n: int) -> list[int]:
+    """Segment bounds hg_cdc_hash uses for an n-byte buffer."""
+    k = hg_cdc_hash_plan(n, None, 0)
+    b = np.zeros(k + 1, dtype=np.uint64)
+    hg_cdc_hash_plan(n, b.ctypes.data, k + 1)
+    return [int(x) for x in b] if k else []
 
 
 def _ptr(t: torch.Tensor | None) -> int | None:
@@ -131,6 +139,21 @@ class Context:
         check(hg_hash_chunks(self.h, algo, _ptr(data), data.numel(), _ptr(ends), nchunk,
                              _ptr(count), _ptr(out), _stream(stream)), "hg_hash_chunks")
         return out
+
+    def cdc_hash(self, data: torch.Tensor, algo: int = MD5, p: hg_cdc_params | None = None,
+                 out=None, stream=None):
+        """Pipelined boundaries + digests (hg_cdc_hash). Returns (ends, count, digests)."""
+        p = p or default_params()
+        n = data.numel()
+        cap = n // p.min_chunk + 2
+        if out is None:
+            out = (torch.empty(cap, dtype=torch.int64, device=self.device),
+                   torch.zeros(1, dtype=torch.int64, device=self.device),
+                   torch.empty((cap, DIGEST_LEN[algo]), dtype=torch.uint8, device=self.device))
+        ends, count, dg = out
+        check(hg_cdc_hash(self.h, algo, _ptr(data), n, p, _ptr(ends), ends.numel(), _ptr(count),
+                          _ptr(dg), _stream(stream)), "hg_cdc_hash")
+        return ends, count, dg
 
     def cdc(self, data: torch.Tensor, algo: int = MD5, p: hg_cdc_params | None = None,
             stream=None):

@@ -72,6 +72,8 @@ SIGNATURES = {
     "hg_cdc_candidates": (_i32, [_vp, _vp, _u64, C.POINTER(hg_cdc_params), _vp, _u64, _vp, _vp]),
     "hg_cdc_boundaries": (_i32, [_vp, _vp, _u64, C.POINTER(hg_cdc_params), _vp, _u64, _vp, _vp]),
     "hg_hash_chunks": (_i32, [_vp, _i32, _vp, _u64, _vp, _u64, _vp, _vp, _vp]),
+    "hg_cdc_hash": (_i32, [_vp, _i32, _vp, _u64, C.POINTER(hg_cdc_params), _vp, _u64, _vp, _vp, _vp]),
+    "hg_cdc_hash_plan": (_u32, [_u64, _vp, _u32]),
     "hg_batch_create": (_i32, [_vp, _vp, _u32, C.POINTER(hg_cdc_params), C.POINTER(_vp)]),
     "hg_batch_destroy": (_i32, [_vp]),
     "hg_batch_slots": (_u64, [_vp, _vp]),
@@ -267,3 +269,12 @@ def hg_server_replay(srv, reqs_ptr, arrivals_ptr, nreq, lat_ptr) -> tuple[int, i
     span = C.c_uint64()
     rc = lib.hg_server_replay(srv, reqs_ptr, arrivals_ptr, nreq, lat_ptr, C.byref(span))
     return rc, span.value
+
+
+def hg_cdc_hash(ctx, algo, d_in, n, params, d_ends, cap, d_count, d_digests, stream) -> int:
+    return lib.hg_cdc_hash(ctx, algo, d_in, n, C.byref(params), d_ends, cap, d_count, d_digests,
+                           stream)
+
+
+def hg_cdc_hash_plan(n, bounds_ptr, max_n) -> int:
+    return lib.hg_cdc_hash_plan(n, bounds_ptr, max_n)

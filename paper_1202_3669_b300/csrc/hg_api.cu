@@ -1,8 +1,10 @@
 // C ABI of libhashgpu.so: argument checks, scratch management and launches.
 // Every computation is done by the kernels in hg_direct.cu and hg_cdc.cu.
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "hg_internal.h"
 
@@ -42,6 +44,7 @@ int ensure(hg_ctx *ctx, void **p, uint64_t *cap, uint64_t count, size_t elem) {
     *p = q;
     *cap = want;
     ctx->held += (size_t)want * elem;
+    ctx->scratch_gen++;
     return HG_OK;
 }
 
@@ -136,6 +139,21 @@ int hg_destroy(hg_ctx *c) {
     cudaFree(c->d_tile_off);
     cudaFree(c->d_cands);
     cudaFree(c->d_err);
+    if (c->pipe_ready) {
+        if (c->p_exec) cudaGraphExecDestroy(c->p_exec);
+        cudaStreamDestroy(c->p_cap);
+        cudaFree(c->d_pipe);
+        cudaStreamDestroy(c->p_win);
+        cudaStreamDestroy(c->p_sel);
+        cudaEventDestroy(c->p_fork);
+        cudaEventDestroy(c->p_done_sel);
+        for (int i = 0; i < kMaxSeg; i++) {
+            cudaStreamDestroy(c->p_hash[i]);
+            cudaEventDestroy(c->p_join[i]);
+            cudaEventDestroy(c->p_ev_win[i]);
+            cudaEventDestroy(c->p_ev_sel[i]);
+        }
+    }
     delete c;
     return HG_OK;
 }
@@ -222,6 +240,152 @@ int hg_cdc_boundaries(hg_ctx *c, const uint8_t *d_in, uint64_t n, const hg_cdc_p
         return r;
     return launch_select(c->d_cands, c->d_ncand, c->cand_cap, c->d_bitmap, n, *p, d_ends, cap,
                          d_count, s);
+}
+
+}  // extern "C"
+
+namespace hg {
+
+static int pipe_setup(hg_ctx *c) {
+    if (c->pipe_ready) return HG_OK;
+    int least = 0, greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    bool ok = cudaStreamCreateWithPriority(&c->p_win, cudaStreamNonBlocking, least) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&c->p_cap, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithPriority(&c->p_sel, cudaStreamNonBlocking, greatest) == cudaSuccess &&
+              cudaEventCreateWithFlags(&c->p_fork, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&c->p_done_sel, cudaEventDisableTiming) == cudaSuccess &&
+              cudaMalloc(&c->d_pipe, sizeof(PipeState)) == cudaSuccess;
+    for (int i = 0; ok && i < kMaxSeg; i++)   // one digest stream per segment: they never wait on each other
+        ok = cudaStreamCreateWithPriority(&c->p_hash[i], cudaStreamNonBlocking, greatest) == cudaSuccess &&
+             cudaEventCreateWithFlags(&c->p_join[i], cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; ok && i < kMaxSeg; i++)
+        ok = cudaEventCreateWithFlags(&c->p_ev_win[i], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&c->p_ev_sel[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        return HG_ECUDA;
+    }
+    c->held += sizeof(PipeState);
+    c->pipe_ready = true;
+    return HG_OK;
+}
+
+// Segment bounds for chunking n bytes: one segment up to 64 MiB; above that,
+// segments of at least 32 MiB (at most 64 of them), each decided and digested
+// while the next is window-hashed. Inner bounds are tile multiples.
+static std::vector<uint64_t> pipe_bounds(uint64_t n) {
+    std::vector<uint64_t> b{0};
+    if (n > (64ull << 20)) {
+        const uint64_t seg = std::max<uint64_t>(32ull << 20, ((n / 60 + kWinTile - 1) / kWinTile) * kWinTile);
+        for (uint64_t x = seg; x + seg / 2 < n; x += seg) b.push_back(x);
+    }
+    b.push_back(n);
+    return b;
+}
+
+}  // namespace hg
+
+extern "C" {
+
+uint32_t hg_cdc_hash_plan(uint64_t n, uint64_t *bounds, uint32_t max) {
+    if (n == 0) return 0;
+    const std::vector<uint64_t> b = pipe_bounds(n);
+    if (bounds)
+        for (uint32_t i = 0; i < b.size() && i < max; i++) bounds[i] = b[i];
+    return (uint32_t)(b.size() - 1);
+}
+
+}  // extern "C"
+
+namespace hg {
+
+// Enqueue the whole pipeline, forked from and joined back into stream s.
+static int enqueue_cdc_hash(hg_ctx *c, int algo, const uint8_t *d_in, uint64_t n,
+                            const hg_cdc_params *p, uint64_t *d_ends, uint64_t cap,
+                            uint64_t *d_count, uint8_t *d_digests, cudaStream_t s) {
+    const std::vector<uint64_t> b = pipe_bounds(n);
+    const int nseg = (int)b.size() - 1;
+    if (nseg > kMaxSeg) return HG_EUNSUPPORTED;
+    PipeBufs pb{c->d_bitmap, c->d_tile_cnt, c->d_tile_off, c->d_cands, c->cand_cap,
+                d_ends, cap, d_digests, (PipeState *)c->d_pipe, c->d_err};
+    int r;
+    cudaEventRecord(c->p_fork, s);
+    cudaStreamWaitEvent(c->p_win, c->p_fork, 0);
+    cudaStreamWaitEvent(c->p_sel, c->p_fork, 0);
+    for (int i = 0; i < nseg; i++) cudaStreamWaitEvent(c->p_hash[i], c->p_fork, 0);
+    if (cudaMemsetAsync(c->d_pipe, 0, sizeof(PipeState), c->p_sel) != cudaSuccess) return HG_ECUDA;
+    for (int k = 0; k < nseg; k++) {
+        const uint64_t lo = b[k], hi = b[k + 1];
+        const uint32_t t0 = (uint32_t)(lo / kWinTile);
+        const uint32_t nt = (uint32_t)((hi + kWinTile - 1) / kWinTile - t0);
+        const uint64_t L = (k == nseg - 1) ? n : hi;
+        const uint64_t max_chunks = (hi - lo + p->max_chunk) / p->min_chunk + 2;
+        if ((r = launch_pipe_segment(d_in, n, *p, algo, t0, nt, L, k, max_chunks, pb, c->p_win,
+                                     c->p_sel, c->p_hash[k], c->p_ev_win[k], c->p_ev_sel[k])))
+            return r;
+    }
+    cudaEventRecord(c->p_done_sel, c->p_sel);
+    cudaStreamWaitEvent(s, c->p_done_sel, 0);
+    cudaEventRecord(c->p_done_sel, c->p_win);
+    cudaStreamWaitEvent(s, c->p_done_sel, 0);
+    for (int i = 0; i < nseg; i++) {
+        cudaEventRecord(c->p_join[i], c->p_hash[i]);
+        cudaStreamWaitEvent(s, c->p_join[i], 0);
+    }
+    return cuda_status(cudaMemcpyAsync(d_count, &((PipeState *)c->d_pipe)->count, sizeof(uint64_t),
+                                       cudaMemcpyDeviceToDevice, s));
+}
+
+}  // namespace hg
+
+extern "C" {
+
+int hg_cdc_hash(hg_ctx *c, int algo, const uint8_t *d_in, uint64_t n, const hg_cdc_params *p,
+                uint64_t *d_ends, uint64_t cap, uint64_t *d_count, uint8_t *d_digests,
+                void *stream) {
+    if (!c || !d_count || hg_digest_len(algo) < 0) return HG_EINVAL;
+    int r = check_params(p);
+    if (r) return r;
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n == 0) return cuda_status(cudaMemsetAsync(d_count, 0, sizeof(uint64_t), s));
+    if (!d_in || !d_ends || !d_digests || (reinterpret_cast<uintptr_t>(d_digests) & 3))
+        return HG_EINVAL;
+    if (cap < n / p->min_chunk + 1) return HG_ECAPACITY;
+    if ((r = ensure_cdc(c, n)) || (r = pipe_setup(c))) return r;
+    // the pipeline (about five launches per segment) is captured once into a
+    // CUDA graph and replayed while its arguments and the scratch stay the same
+    const uint64_t key[16] = {(uint64_t)(uintptr_t)d_in, n, p->window, p->mask_bits, p->magic,
+                              p->min_chunk, p->max_chunk, (uint64_t)algo,
+                              (uint64_t)(uintptr_t)d_ends, cap, (uint64_t)(uintptr_t)d_count,
+                              (uint64_t)(uintptr_t)d_digests, c->scratch_gen, 1, 0, 0};
+    if (!c->p_exec || std::memcmp(key, c->p_key, sizeof key)) {
+        if (c->p_exec) {
+            cudaStreamSynchronize(s);
+            cudaGraphExecDestroy(c->p_exec);
+            c->p_exec = nullptr;
+        }
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(c->p_cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return HG_ECUDA;
+        r = enqueue_cdc_hash(c, algo, d_in, n, p, d_ends, cap, d_count, d_digests, c->p_cap);
+        const cudaError_t e = cudaStreamEndCapture(c->p_cap, &graph);
+        if (r || e != cudaSuccess) {
+            cudaGetLastError();
+            if (graph) cudaGraphDestroy(graph);
+            return r ? r : HG_ECUDA;
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&c->p_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) {
+            cudaGetLastError();
+            c->p_exec = nullptr;
+            return HG_ECUDA;
+        }
+        std::memcpy(c->p_key, key, sizeof key);
+    }
+    return cuda_status(cudaGraphLaunch(c->p_exec, s));
 }
 
 int hg_hash_chunks(hg_ctx *c, int algo, const uint8_t *d_in, uint64_t n, const uint64_t *d_ends,

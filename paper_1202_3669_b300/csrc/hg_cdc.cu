@@ -24,14 +24,15 @@ __global__ void __launch_bounds__(kWinThreads) k_window_bitmap(const uint8_t *__
                                                                uint32_t mask, uint32_t magic,
                                                                uint32_t *__restrict__ bitmap,
                                                                uint32_t *__restrict__ tile_cnt,
-                                                               int *err) {
+                                                               int *err, uint32_t tile0) {
     const uint32_t wlen = W ? (uint32_t)W : wrt;
     __shared__ __align__(128) uint8_t sbuf[kSmemBytes];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t warp_cnt[kWinThreads / 32];
 
     const int t = threadIdx.x;
-    const uint64_t tile = (uint64_t)blockIdx.x * kWinTile;
+    const uint32_t tix = blockIdx.x + tile0;
+    const uint64_t tile = (uint64_t)tix * kWinTile;
     const bool fast = ((reinterpret_cast<uintptr_t>(in) & 15) == 0) && tile >= (uint64_t)kHalo &&
                       tile + kWinTile <= n;
     if (t < 4) reinterpret_cast<uint32_t *>(sbuf + kHalo + kWinTile)[t] = 0;
@@ -67,7 +68,7 @@ __global__ void __launch_bounds__(kWinThreads) k_window_bitmap(const uint8_t *__
         uint32_t s = 0;
 #pragma unroll
         for (int w = 0; w < kWinThreads / 32; w++) s += warp_cnt[w];
-        tile_cnt[blockIdx.x] = s;
+        tile_cnt[tix] = s;
     }
 }
 
@@ -108,6 +109,45 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(const uint32_t *__restrict_
     if (t == 1023) *total = run;
 }
 
+// Exclusive scan of the counts of tiles [0, ntiles) of a segment, added to the
+// running candidate count *total (read first, updated at the end), one CTA.
+__global__ void __launch_bounds__(1024) k_scan_tiles_base(const uint32_t *__restrict__ cnt,
+                                                          uint64_t ntiles, uint64_t *__restrict__ off,
+                                                          uint64_t *total) {
+    __shared__ uint64_t warp_sum[32];
+    __shared__ uint64_t s_base;
+    const int t = threadIdx.x;
+    if (t == 0) s_base = *total;
+    const uint64_t per = (ntiles + 1023) / 1024;
+    const uint64_t a = min(ntiles, per * t), b = min(ntiles, per * (t + 1));
+    uint64_t s = 0;
+    for (uint64_t i = a; i < b; i++) s += cnt[i];
+    uint64_t x = s;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xffffffffu, x, d);
+        if ((t & 31) >= d) x += y;
+    }
+    if ((t & 31) == 31) warp_sum[t >> 5] = x;
+    __syncthreads();
+    if (t < 32) {
+        uint64_t w = warp_sum[t];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint64_t y = __shfl_up_sync(0xffffffffu, w, d);
+            if (t >= d) w += y;
+        }
+        warp_sum[t] = w;
+    }
+    __syncthreads();
+    uint64_t run = s_base + x - s + ((t >> 5) ? warp_sum[(t >> 5) - 1] : 0);
+    for (uint64_t i = a; i < b; i++) {
+        off[i] = run;
+        run += cnt[i];
+    }
+    if (t == 1023) *total = run;
+}
+
 // Bitmap -> increasing cut positions. One CTA per window tile; tiles without
 // candidates leave at once.
 __global__ void __launch_bounds__(kWinThreads) k_compact(const uint32_t *__restrict__ bitmap,
@@ -115,11 +155,12 @@ __global__ void __launch_bounds__(kWinThreads) k_compact(const uint32_t *__restr
                                                          const uint32_t *__restrict__ tile_cnt,
                                                          const uint64_t *__restrict__ tile_off,
                                                          uint64_t *__restrict__ cands,
-                                                         uint64_t cap) {
+                                                         uint64_t cap, uint32_t tile0) {
     __shared__ uint32_t warp_sum[kWinThreads / 32];
-    if (tile_cnt[blockIdx.x] == 0) return;
+    const uint32_t tix = blockIdx.x + tile0;
+    if (tile_cnt[tix] == 0) return;
     const int t = threadIdx.x;
-    const uint64_t widx = (uint64_t)blockIdx.x * kWinThreads + t;
+    const uint64_t widx = (uint64_t)tix * kWinThreads + t;
     uint32_t w = widx < nwords ? bitmap[widx] : 0u;
     const uint32_t c = __popc(w);
     uint32_t x = c;
@@ -132,7 +173,7 @@ __global__ void __launch_bounds__(kWinThreads) k_compact(const uint32_t *__restr
     __syncthreads();
     uint32_t before = x - c;
     for (int k = 0; k < (t >> 5); k++) before += warp_sum[k];
-    uint64_t idx = tile_off[blockIdx.x] + before;
+    uint64_t idx = tile_off[tix] + before;
     const uint64_t pos0 = widx * 32;
     while (w) {
         const int b = __ffs(w) - 1;
@@ -209,6 +250,73 @@ __device__ void select_serial(const uint64_t *__restrict__ cands, uint64_t ncand
     if (lane == 0) *d_count = count;
 }
 
+// Selection for one segment of a pipelined chunking: candidates are known up to
+// L (the segment's end; L = n for the last one). Starts from the carried chunk
+// start, appends every cut the known candidates decide, and carries the start
+// of the still-open chunk to the next segment.
+__global__ void __launch_bounds__(kSelThreads) k_select_seg(
+    const uint64_t *__restrict__ cands, uint64_t cand_cap, const uint32_t *__restrict__ bitmap,
+    uint64_t n, uint64_t L, uint64_t mn, uint64_t mx, uint64_t *__restrict__ ends, uint64_t cap,
+    PipeState *st, int seg) {
+    __shared__ uint64_t s_carry, s_count, s_ncand, s_new;
+    __shared__ uint32_t s_k0;
+    const int t = threadIdx.x;
+    if (t == 0) {
+        s_carry = st->carry;
+        s_count = st->count;
+        s_ncand = st->ncand;
+        uint32_t k0 = 0;
+        if (s_ncand <= cand_cap && s_ncand < 0xffffffffull) {
+            uint32_t hi = (uint32_t)s_ncand;                  // first candidate > carry
+            while (k0 < hi) {
+                const uint32_t mid = k0 + (hi - k0) / 2;
+                if (cands[mid] > s_carry) hi = mid; else k0 = mid + 1;
+            }
+        }
+        s_k0 = k0;
+        s_new = 0;
+    }
+    __syncthreads();
+    const uint64_t count = s_count, carry = s_carry;
+    const uint64_t room = cap > count ? cap - count : 0;
+    if (s_ncand > cand_cap || s_ncand >= 0xffffffffull) {
+        if (t == 0) {
+            uint64_t idx = 0;
+            const uint64_t last = select_thread_bitmap(bitmap, carry, n, mn, mx,
+                                                       WriteEmit{ends + count, room, &idx, 0}, L);
+            st->count = count + idx;
+            st->carry = last;
+            st->seg_cnt[seg + 1] = count + idx;
+        }
+        return;
+    }
+    const uint32_t k0 = s_k0;
+    select_block(cands + k0, (uint32_t)(s_ncand - k0), carry, n, mn, mx, ends + count, room, &s_new,
+                 L, 0);
+    __syncthreads();
+    if (t == 0) {
+        const uint64_t nw = s_new;
+        st->count = count + nw;
+        st->carry = nw ? ends[count + nw - 1] : carry;
+        st->seg_cnt[seg + 1] = count + nw;
+    }
+}
+
+// Digests of the chunks one segment's selection finalized.
+template <class H>
+__global__ void __launch_bounds__(128) k_hash_seg(const uint8_t *__restrict__ in,
+                                                  const uint64_t *__restrict__ ends,
+                                                  const PipeState *st, int seg,
+                                                  uint8_t *__restrict__ out) {
+    const uint64_t lo = st->seg_cnt[seg], hi = st->seg_cnt[seg + 1];
+    const uint64_t i = lo + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= hi) return;
+    const uint64_t a = i ? ends[i - 1] : 0, b = ends[i];
+    H hs;
+    hash_range(in + a, b - a, hs);
+    store_digest(hs, out + i * H::kDigest);
+}
+
 // Selection of the whole stream by one CTA (parallel, exact); when the
 // candidate list overflowed, warp 0 walks the bitmap instead.
 __global__ void __launch_bounds__(kSelThreads) k_select_par(
@@ -226,29 +334,35 @@ __global__ void __launch_bounds__(kSelThreads) k_select_par(
 template <int W>
 void launch_window_t(const uint8_t *d_in, uint64_t n, uint32_t w, uint32_t mask, uint32_t magic,
                      uint32_t *d_bitmap, uint32_t *d_tile_cnt, uint64_t ntiles, cudaStream_t s,
-                     int *d_err) {
+                     int *d_err, uint32_t tile0) {
     k_window_bitmap<W><<<(unsigned)ntiles, kWinThreads, 0, s>>>(d_in, n, w, mask, magic, d_bitmap,
-                                                                 d_tile_cnt, d_err);
+                                                                 d_tile_cnt, d_err, tile0);
 }
 
 }  // namespace
 
 int launch_window_bitmap(const uint8_t *d_in, uint64_t n, const hg_cdc_params &p,
                          uint32_t *d_bitmap, uint32_t *d_tile_cnt, cudaStream_t s, int *d_err) {
-    const uint64_t ntiles = (n + kWinTile - 1) / kWinTile;
+    return launch_window_range(d_in, n, p, d_bitmap, d_tile_cnt, 0, (n + kWinTile - 1) / kWinTile, s,
+                               d_err);
+}
+
+int launch_window_range(const uint8_t *d_in, uint64_t n, const hg_cdc_params &p,
+                        uint32_t *d_bitmap, uint32_t *d_tile_cnt, uint32_t tile0, uint64_t ntiles,
+                        cudaStream_t s, int *d_err) {
     if (ntiles == 0) return HG_OK;
     const uint32_t mask = p.mask_bits >= 32 ? 0xffffffffu : ((1u << p.mask_bits) - 1u);
     if (p.window < 1 || p.window > 55) return HG_EUNSUPPORTED;
     switch (p.window) {
 #define HG_W(w)                                                                                \
     case w:                                                                                    \
-        launch_window_t<w>(d_in, n, w, mask, p.magic, d_bitmap, d_tile_cnt, ntiles, s, d_err); \
+        launch_window_t<w>(d_in, n, w, mask, p.magic, d_bitmap, d_tile_cnt, ntiles, s, d_err, tile0); \
         break;
         HG_W(16) HG_W(20) HG_W(24) HG_W(32) HG_W(48)
 #undef HG_W
         default:
             launch_window_t<0>(d_in, n, p.window, mask, p.magic, d_bitmap, d_tile_cnt, ntiles, s,
-                               d_err);
+                               d_err, tile0);
     }
     return cuda_status(cudaGetLastError());
 }
@@ -259,7 +373,34 @@ int launch_compact(const uint32_t *d_bitmap, uint64_t n, const uint32_t *d_tile_
     if (ntiles == 0) return cuda_status(cudaMemsetAsync(d_count, 0, sizeof(uint64_t), s));
     k_scan_tiles<<<1, 1024, 0, s>>>(d_tile_cnt, ntiles, d_tile_off, d_count);
     k_compact<<<(unsigned)ntiles, kWinThreads, 0, s>>>(d_bitmap, (n + 31) / 32, d_tile_cnt,
-                                                       d_tile_off, d_cands, cap);
+                                                       d_tile_off, d_cands, cap, 0);
+    return cuda_status(cudaGetLastError());
+}
+
+int launch_pipe_segment(const uint8_t *d_in, uint64_t n, const hg_cdc_params &p, int algo,
+                        uint32_t tile0, uint32_t ntiles, uint64_t L, int seg, uint64_t max_chunks,
+                        const PipeBufs &b, cudaStream_t s_win, cudaStream_t s_sel,
+                        cudaStream_t s_hash, cudaEvent_t ev_win, cudaEvent_t ev_sel) {
+    // windows run back to back on s_win; the small serial steps (scan, compaction,
+    // selection) of segment k run on s_sel, in segment order, once its windows are done
+    int r;
+    if ((r = launch_window_range(d_in, n, p, b.bitmap, b.tile_cnt, tile0, ntiles, s_win, b.err)))
+        return r;
+    cudaEventRecord(ev_win, s_win);
+    cudaStreamWaitEvent(s_sel, ev_win, 0);
+    k_scan_tiles_base<<<1, 1024, 0, s_sel>>>(b.tile_cnt + tile0, ntiles, b.tile_off + tile0,
+                                             &b.st->ncand);
+    k_compact<<<ntiles, kWinThreads, 0, s_sel>>>(b.bitmap, (n + 31) / 32, b.tile_cnt, b.tile_off,
+                                                 b.cands, b.cand_cap, tile0);
+    k_select_seg<<<1, kSelThreads, 0, s_sel>>>(b.cands, b.cand_cap, b.bitmap, n, L, p.min_chunk,
+                                               p.max_chunk, b.ends, b.cap, b.st, seg);
+    cudaEventRecord(ev_sel, s_sel);
+    cudaStreamWaitEvent(s_hash, ev_sel, 0);
+    const unsigned grid = (unsigned)((max_chunks + 127) / 128);
+    if (algo == HG_MD5)
+        k_hash_seg<Md5Chain><<<grid, 128, 0, s_hash>>>(d_in, b.ends, b.st, seg, b.digests);
+    else
+        k_hash_seg<Sha1><<<grid, 128, 0, s_hash>>>(d_in, b.ends, b.st, seg, b.digests);
     return cuda_status(cudaGetLastError());
 }
 

@@ -129,6 +129,100 @@ struct Md5 {
     __device__ __forceinline__ uint32_t out_word(int i) const { return h[i]; }
 };
 
+// MD5 with every operation written so the serial chain is as short as the
+// hardware allows: a + M + T is formed off the chain, then one add of F, one
+// wrap-around shift and one add of b. Used where one long message is the
+// critical path (chunk digests, the hash-of-hashes); the throughput kernels
+// keep Md5, whose form compiles to fewer instructions.
+#define HG_MD5_CSTEP(f, a, b, c, d, m, k, s)                                                    \
+    do {                                                                                        \
+        const uint32_t fv_ = f((b), (c), (d));                                                  \
+        const uint32_t t_ = (a) + (m) + (uint32_t)(k);                                          \
+        uint32_t u_, r_;                                                                        \
+        asm("add.u32 %0, %1, %2;" : "=r"(u_) : "r"(t_), "r"(fv_));                              \
+        asm("shf.l.wrap.b32 %0, %1, %1, %2;" : "=r"(r_) : "r"(u_), "n"(s));                      \
+        (a) = r_ + (b);                                                                         \
+    } while (0)
+
+__device__ __forceinline__ void md5_rounds_chain(uint32_t &a, uint32_t &b, uint32_t &c, uint32_t &d,
+                                                 const uint32_t (&M)[16]) {
+    HG_MD5_CSTEP(HG_MD5_F, a, b, c, d, M[0], 0xd76aa478, 7);
+    HG_MD5_CSTEP(HG_MD5_F, d, a, b, c, M[1], 0xe8c7b756, 12);
+    HG_MD5_CSTEP(HG_MD5_F, c, d, a, b, M[2], 0x242070db, 17);
+    HG_MD5_CSTEP(HG_MD5_F, b, c, d, a, M[3], 0xc1bdceee, 22);
+    HG_MD5_CSTEP(HG_MD5_F, a, b, c, d, M[4], 0xf57c0faf, 7);
+    HG_MD5_CSTEP(HG_MD5_F, d, a, b, c, M[5], 0x4787c62a, 12);
+    HG_MD5_CSTEP(HG_MD5_F, c, d, a, b, M[6], 0xa8304613, 17);
+    HG_MD5_CSTEP(HG_MD5_F, b, c, d, a, M[7], 0xfd469501, 22);
+    HG_MD5_CSTEP(HG_MD5_F, a, b, c, d, M[8], 0x698098d8, 7);
+    HG_MD5_CSTEP(HG_MD5_F, d, a, b, c, M[9], 0x8b44f7af, 12);
+    HG_MD5_CSTEP(HG_MD5_F, c, d, a, b, M[10], 0xffff5bb1, 17);
+    HG_MD5_CSTEP(HG_MD5_F, b, c, d, a, M[11], 0x895cd7be, 22);
+    HG_MD5_CSTEP(HG_MD5_F, a, b, c, d, M[12], 0x6b901122, 7);
+    HG_MD5_CSTEP(HG_MD5_F, d, a, b, c, M[13], 0xfd987193, 12);
+    HG_MD5_CSTEP(HG_MD5_F, c, d, a, b, M[14], 0xa679438e, 17);
+    HG_MD5_CSTEP(HG_MD5_F, b, c, d, a, M[15], 0x49b40821, 22);
+
+    HG_MD5_CSTEP(HG_MD5_G, a, b, c, d, M[1], 0xf61e2562, 5);
+    HG_MD5_CSTEP(HG_MD5_G, d, a, b, c, M[6], 0xc040b340, 9);
+    HG_MD5_CSTEP(HG_MD5_G, c, d, a, b, M[11], 0x265e5a51, 14);
+    HG_MD5_CSTEP(HG_MD5_G, b, c, d, a, M[0], 0xe9b6c7aa, 20);
+    HG_MD5_CSTEP(HG_MD5_G, a, b, c, d, M[5], 0xd62f105d, 5);
+    HG_MD5_CSTEP(HG_MD5_G, d, a, b, c, M[10], 0x02441453, 9);
+    HG_MD5_CSTEP(HG_MD5_G, c, d, a, b, M[15], 0xd8a1e681, 14);
+    HG_MD5_CSTEP(HG_MD5_G, b, c, d, a, M[4], 0xe7d3fbc8, 20);
+    HG_MD5_CSTEP(HG_MD5_G, a, b, c, d, M[9], 0x21e1cde6, 5);
+    HG_MD5_CSTEP(HG_MD5_G, d, a, b, c, M[14], 0xc33707d6, 9);
+    HG_MD5_CSTEP(HG_MD5_G, c, d, a, b, M[3], 0xf4d50d87, 14);
+    HG_MD5_CSTEP(HG_MD5_G, b, c, d, a, M[8], 0x455a14ed, 20);
+    HG_MD5_CSTEP(HG_MD5_G, a, b, c, d, M[13], 0xa9e3e905, 5);
+    HG_MD5_CSTEP(HG_MD5_G, d, a, b, c, M[2], 0xfcefa3f8, 9);
+    HG_MD5_CSTEP(HG_MD5_G, c, d, a, b, M[7], 0x676f02d9, 14);
+    HG_MD5_CSTEP(HG_MD5_G, b, c, d, a, M[12], 0x8d2a4c8a, 20);
+
+    HG_MD5_CSTEP(HG_MD5_H, a, b, c, d, M[5], 0xfffa3942, 4);
+    HG_MD5_CSTEP(HG_MD5_H, d, a, b, c, M[8], 0x8771f681, 11);
+    HG_MD5_CSTEP(HG_MD5_H, c, d, a, b, M[11], 0x6d9d6122, 16);
+    HG_MD5_CSTEP(HG_MD5_H, b, c, d, a, M[14], 0xfde5380c, 23);
+    HG_MD5_CSTEP(HG_MD5_H, a, b, c, d, M[1], 0xa4beea44, 4);
+    HG_MD5_CSTEP(HG_MD5_H, d, a, b, c, M[4], 0x4bdecfa9, 11);
+    HG_MD5_CSTEP(HG_MD5_H, c, d, a, b, M[7], 0xf6bb4b60, 16);
+    HG_MD5_CSTEP(HG_MD5_H, b, c, d, a, M[10], 0xbebfbc70, 23);
+    HG_MD5_CSTEP(HG_MD5_H, a, b, c, d, M[13], 0x289b7ec6, 4);
+    HG_MD5_CSTEP(HG_MD5_H, d, a, b, c, M[0], 0xeaa127fa, 11);
+    HG_MD5_CSTEP(HG_MD5_H, c, d, a, b, M[3], 0xd4ef3085, 16);
+    HG_MD5_CSTEP(HG_MD5_H, b, c, d, a, M[6], 0x04881d05, 23);
+    HG_MD5_CSTEP(HG_MD5_H, a, b, c, d, M[9], 0xd9d4d039, 4);
+    HG_MD5_CSTEP(HG_MD5_H, d, a, b, c, M[12], 0xe6db99e5, 11);
+    HG_MD5_CSTEP(HG_MD5_H, c, d, a, b, M[15], 0x1fa27cf8, 16);
+    HG_MD5_CSTEP(HG_MD5_H, b, c, d, a, M[2], 0xc4ac5665, 23);
+
+    HG_MD5_CSTEP(HG_MD5_I, a, b, c, d, M[0], 0xf4292244, 6);
+    HG_MD5_CSTEP(HG_MD5_I, d, a, b, c, M[7], 0x432aff97, 10);
+    HG_MD5_CSTEP(HG_MD5_I, c, d, a, b, M[14], 0xab9423a7, 15);
+    HG_MD5_CSTEP(HG_MD5_I, b, c, d, a, M[5], 0xfc93a039, 21);
+    HG_MD5_CSTEP(HG_MD5_I, a, b, c, d, M[12], 0x655b59c3, 6);
+    HG_MD5_CSTEP(HG_MD5_I, d, a, b, c, M[3], 0x8f0ccc92, 10);
+    HG_MD5_CSTEP(HG_MD5_I, c, d, a, b, M[10], 0xffeff47d, 15);
+    HG_MD5_CSTEP(HG_MD5_I, b, c, d, a, M[1], 0x85845dd1, 21);
+    HG_MD5_CSTEP(HG_MD5_I, a, b, c, d, M[8], 0x6fa87e4f, 6);
+    HG_MD5_CSTEP(HG_MD5_I, d, a, b, c, M[15], 0xfe2ce6e0, 10);
+    HG_MD5_CSTEP(HG_MD5_I, c, d, a, b, M[6], 0xa3014314, 15);
+    HG_MD5_CSTEP(HG_MD5_I, b, c, d, a, M[13], 0x4e0811a1, 21);
+    HG_MD5_CSTEP(HG_MD5_I, a, b, c, d, M[4], 0xf7537e82, 6);
+    HG_MD5_CSTEP(HG_MD5_I, d, a, b, c, M[11], 0xbd3af235, 10);
+    HG_MD5_CSTEP(HG_MD5_I, c, d, a, b, M[2], 0x2ad7d2bb, 15);
+    HG_MD5_CSTEP(HG_MD5_I, b, c, d, a, M[9], 0xeb86d391, 21);
+}
+
+struct Md5Chain : Md5 {
+    __device__ __forceinline__ void compress(const uint32_t (&M)[16]) {
+        uint32_t a = h[0], b = h[1], c = h[2], d = h[3];
+        md5_rounds_chain(a, b, c, d, M);
+        h[0] += a; h[1] += b; h[2] += c; h[3] += d;
+    }
+};
+
 // --------------------------------------------------------------- SHA-1 -----
 
 struct Sha1 {

@@ -88,7 +88,7 @@ __global__ void k_multi_roots(const BlkReq *__restrict__ reqs, uint32_t nreq) {
     const BlkReq r = reqs[k];
     const uint64_t nblk = (r.len + r.block - 1) / r.block;
     if (r.algo == HG_MD5) {
-        Md5 hs;
+        Md5Chain hs;
         hash_range(r.out, nblk * Md5::kDigest, hs);
         store_digest(hs, r.out + nblk * Md5::kDigest);
     } else {
@@ -120,7 +120,7 @@ int launch_hash_blocks(int algo, const uint8_t *d_in, uint64_t n, uint64_t block
 
 int launch_root(int algo, const uint8_t *d_digests, uint64_t nbytes, uint8_t *d_root,
                 cudaStream_t s) {
-    if (algo == HG_MD5) k_root<Md5><<<1, 32, 0, s>>>(d_digests, nbytes, d_root);
+    if (algo == HG_MD5) k_root<Md5Chain><<<1, 32, 0, s>>>(d_digests, nbytes, d_root);
     else k_root<Sha1><<<1, 32, 0, s>>>(d_digests, nbytes, d_root);
     return cuda_status(cudaGetLastError());
 }
@@ -131,7 +131,7 @@ int launch_hash_chunks(int algo, const uint8_t *d_in, uint64_t n, const uint64_t
     if (nchunk == 0) return HG_OK;
     const unsigned grid = (unsigned)((nchunk + 127) / 128);
     if (algo == HG_MD5)
-        k_hash_chunks<Md5><<<grid, 128, 0, s>>>(d_in, n, d_ends, nchunk, d_count, d_digests, d_err);
+        k_hash_chunks<Md5Chain><<<grid, 128, 0, s>>>(d_in, n, d_ends, nchunk, d_count, d_digests, d_err);
     else
         k_hash_chunks<Sha1><<<grid, 128, 0, s>>>(d_in, n, d_ends, nchunk, d_count, d_digests, d_err);
     return cuda_status(cudaGetLastError());

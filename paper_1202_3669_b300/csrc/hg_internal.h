@@ -19,6 +19,16 @@ struct hg_ctx {
     uint64_t *d_tile_off = nullptr;  uint64_t tile_off_cap = 0;
     uint64_t *d_cands = nullptr;     uint64_t cand_cap = 0;
     uint64_t *d_ncand = nullptr;     // one word
+    // pipelined chunking (hg_cdc_hash): streams, events, device state
+    bool pipe_ready = false;
+    cudaStream_t p_win = nullptr, p_sel = nullptr, p_hash[64] = {};
+    cudaEvent_t p_fork = nullptr, p_done_sel = nullptr, p_join[64] = {};
+    cudaEvent_t p_ev_win[64] = {}, p_ev_sel[64] = {};
+    void *d_pipe = nullptr;
+    cudaStream_t p_cap = nullptr;           // capture origin of the pipeline graph
+    cudaGraphExec_t p_exec = nullptr;       // replayed while p_key matches
+    uint64_t p_key[16] = {};
+    uint64_t scratch_gen = 0;               // bumped whenever scratch is reallocated
 };
 
 namespace hg {
@@ -57,12 +67,37 @@ struct BlkReq {
 };
 int launch_multi_blocks(const BlkReq *d_reqs, uint32_t nreq, uint64_t total_blocks, cudaStream_t s);
 
+// Pipelined chunking of one buffer (hg_cdc_hash): device state.
+constexpr int kMaxSeg = 64;
+struct PipeState {
+    uint64_t carry;      // start of the chunk still open after the last segment
+    uint64_t count;      // chunks finalized so far
+    uint64_t ncand;      // candidates found so far
+    uint64_t pad;
+    uint64_t seg_cnt[kMaxSeg + 1];   // chunks finalized after segment k-1 (seg_cnt[0] = 0)
+};
+struct PipeBufs {
+    uint32_t *bitmap, *tile_cnt;
+    uint64_t *tile_off, *cands, cand_cap;
+    uint64_t *ends, cap;
+    uint8_t *digests;
+    PipeState *st;
+    int *err;
+};
+
 // hg_cdc.cu
 int launch_window_bitmap(const uint8_t *d_in, uint64_t n, const hg_cdc_params &p,
                          uint32_t *d_bitmap, uint32_t *d_tile_cnt, cudaStream_t s, int *d_err);
 int launch_compact(const uint32_t *d_bitmap, uint64_t n, const uint32_t *d_tile_cnt,
                    uint64_t *d_tile_off, uint64_t ntiles, uint64_t *d_cands, uint64_t cap,
                    uint64_t *d_count, cudaStream_t s);
+int launch_window_range(const uint8_t *d_in, uint64_t n, const hg_cdc_params &p,
+                        uint32_t *d_bitmap, uint32_t *d_tile_cnt, uint32_t tile0, uint64_t ntiles,
+                        cudaStream_t s, int *d_err);
+int launch_pipe_segment(const uint8_t *d_in, uint64_t n, const hg_cdc_params &p, int algo,
+                        uint32_t tile0, uint32_t ntiles, uint64_t L, int seg, uint64_t max_chunks,
+                        const PipeBufs &b, cudaStream_t s_win, cudaStream_t s_sel,
+                        cudaStream_t s_hash, cudaEvent_t ev_win, cudaEvent_t ev_sel);
 int launch_scan_tiles(const uint32_t *d_tile_cnt, uint64_t ntiles, uint64_t *d_tile_off,
                       uint64_t *d_total, cudaStream_t s);
 int launch_select(const uint64_t *d_cands, const uint64_t *d_ncand, uint64_t cand_cap,
@@ -75,7 +110,7 @@ inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? HG_OK : HG_ECU
 // Files from this size up select their boundaries with a whole CTA.
 constexpr uint64_t kJobBigFileBytes = 1ull << 20;
 // counters of a job (device words)
-enum { kJobTotal = 0, kJobFront = 1, kJobBack = 2, kJobTaskCtr = 3, kJobTileCtr = 4, kJobNumWords = 8 };
+enum { kJobTotal = 0, kJobTaskCtr = 1, kJobTileCtr = 2, kJobHist = 8, kJobNumWords = 8 + 128 };
 
 // Device view of a job: file f is jptr(f) .. + jlen(f): base + file_off[f] when
 // base is set (files back to back), else file_ptr[f] / file_len[f]. Its tiles
@@ -108,7 +143,7 @@ struct JobTuning {
     int window_ctas;       // persistent window CTAs per SM
     int hash_threads;
     int hash_ctas;         // chunk-hash CTAs per SM
-    uint64_t long_bytes;   // chunks at least this long are hashed first
+    uint64_t long_bytes;   // kept for the tuning record; tasks are ordered by length
 };
 
 struct JobHost {

@@ -234,33 +234,63 @@ __global__ void __launch_bounds__(kSelThreads) k_job_select_big(
     if (threadIdx.x == 0) atomicAdd(&words[kJobTotal], (unsigned long long)min(counts[f], cap));
 }
 
-// Task list: long chunks from the front, the rest from the back.
-__global__ void k_job_tasks(JobDev j, const uint64_t *__restrict__ ends,
-                            const uint64_t *__restrict__ counts, uint64_t long_bytes,
-                            unsigned long long *words, uint64_t *__restrict__ tasks) {
+// Task list ordered by chunk length, longest first (counting sort on 1 KiB
+// buckets), so the 32 chunks a warp hashes together have nearly equal serial
+// chains and long chains start first.
+constexpr int kLenBuckets = 64;
+__device__ __forceinline__ int len_bucket(uint64_t len) {
+    const uint64_t b = len >> 10;
+    return (int)(kLenBuckets - 1 - (b < kLenBuckets - 1 ? b : kLenBuckets - 1));   // long first
+}
+
+__global__ void k_job_hist(JobDev j, const uint64_t *__restrict__ ends,
+                           const uint64_t *__restrict__ counts, unsigned long long *hist) {
+    __shared__ unsigned int h[kLenBuckets];
+    for (int i = threadIdx.x; i < kLenBuckets; i += blockDim.x) h[i] = 0;
+    __syncthreads();
     const uint32_t f = blockIdx.x;
     const uint64_t so = j.slot_off[f];
     const uint64_t cnt = min(counts[f], j.slot_off[f + 1] - so);
-    const uint64_t total = words[kJobTotal];
-    const int lane = threadIdx.x & 31;
-    for (uint64_t r = 0; r < cnt; r += blockDim.x) {
-        const uint64_t i = r + threadIdx.x;
-        const bool act = i < cnt;
-        uint64_t len = 0;
-        if (act) len = ends[so + i] - (i ? ends[so + i - 1] : 0);
-        const bool lng = act && len >= long_bytes;
-        const uint32_t ml = __ballot_sync(0xffffffffu, lng);
-        const uint32_t ms = __ballot_sync(0xffffffffu, act && !lng);
-        unsigned long long bl = 0, bs = 0;
-        if (lane == 0) {
-            if (ml) bl = atomicAdd(&words[kJobFront], (unsigned long long)__popc(ml));
-            if (ms) bs = atomicAdd(&words[kJobBack], (unsigned long long)__popc(ms));
-        }
-        bl = __shfl_sync(0xffffffffu, bl, 0);
-        bs = __shfl_sync(0xffffffffu, bs, 0);
-        const uint32_t below = (1u << lane) - 1u;
-        if (lng) tasks[bl + __popc(ml & below)] = ((uint64_t)f << 32) | (uint32_t)i;
-        else if (act) tasks[total - 1 - (bs + __popc(ms & below))] = ((uint64_t)f << 32) | (uint32_t)i;
+    for (uint64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+        const uint64_t len = ends[so + i] - (i ? ends[so + i - 1] : 0);
+        atomicAdd(&h[len_bucket(len)], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kLenBuckets; i += blockDim.x)
+        if (h[i]) atomicAdd(&hist[i], (unsigned long long)h[i]);
+}
+
+// exclusive scan of the bucket counts into cursors (one warp)
+__global__ void k_job_hist_scan(unsigned long long *hist, unsigned long long *cursor) {
+    const int lane = threadIdx.x;
+    unsigned long long a = hist[lane], b = hist[lane + 32];
+    unsigned long long x = a;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+    }
+    const unsigned long long tot_a = __shfl_sync(0xffffffffu, x, 31);
+    unsigned long long z = b;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, z, d);
+        if (lane >= d) z += y;
+    }
+    cursor[lane] = x - a;
+    cursor[lane + 32] = tot_a + z - b;
+}
+
+__global__ void k_job_tasks(JobDev j, const uint64_t *__restrict__ ends,
+                            const uint64_t *__restrict__ counts, unsigned long long *cursor,
+                            uint64_t *__restrict__ tasks) {
+    const uint32_t f = blockIdx.x;
+    const uint64_t so = j.slot_off[f];
+    const uint64_t cnt = min(counts[f], j.slot_off[f + 1] - so);
+    for (uint64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+        const uint64_t len = ends[so + i] - (i ? ends[so + i - 1] : 0);
+        const unsigned long long at = atomicAdd(&cursor[len_bucket(len)], 1ull);
+        tasks[at] = ((uint64_t)f << 32) | (uint32_t)i;
     }
 }
 
@@ -393,11 +423,15 @@ int enqueue_cdc_job(const JobDev &j, const JobScratch &sc, const hg_cdc_params &
         k_job_select_big<<<j.nbig, kSelThreads, 0, s>>>(j, sc.tile_off, sc.cands, sc.cand_cap,
                                                        sc.bitmap, p.min_chunk, p.max_chunk, d_ends,
                                                        d_counts, sc.words);
-    if (j.nfile)
-        k_job_tasks<<<j.nfile, 128, 0, s>>>(j, d_ends, d_counts, tn.long_bytes, sc.words, sc.tasks);
+    if (j.nfile) {
+        unsigned long long *hist = sc.words + kJobHist, *cursor = sc.words + kJobHist + kLenBuckets;
+        k_job_hist<<<j.nfile, 128, 0, s>>>(j, d_ends, d_counts, hist);
+        k_job_hist_scan<<<1, 32, 0, s>>>(hist, cursor);
+        k_job_tasks<<<j.nfile, 128, 0, s>>>(j, d_ends, d_counts, cursor, sc.tasks);
+    }
     const int hgrid = num_sms * tn.hash_ctas;
     if (algo == HG_MD5)
-        k_job_hash<Md5><<<hgrid, tn.hash_threads, 0, s>>>(j, d_ends, sc.tasks, sc.words, d_digests);
+        k_job_hash<Md5Chain><<<hgrid, tn.hash_threads, 0, s>>>(j, d_ends, sc.tasks, sc.words, d_digests);
     else
         k_job_hash<Sha1><<<hgrid, tn.hash_threads, 0, s>>>(j, d_ends, sc.tasks, sc.words, d_digests);
     return cuda_status(cudaGetLastError());

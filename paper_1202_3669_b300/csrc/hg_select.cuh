@@ -16,6 +16,11 @@
 //
 // Positions are absolute offsets into the buffer that holds the stream; the
 // stream occupies [s0, n) and cuts are written relative to s0.
+//
+// A limit L < n says only the candidates up to L are known (a stream being
+// chunked segment by segment): a cut is emitted only when the candidates up to
+// L decide it, and a chain whose next decision needs more stops (returns m)
+// without emitting. L >= n means everything is known.
 #pragma once
 #include <cstdint>
 
@@ -59,9 +64,10 @@ struct WriteEmit {
 
 // One chain step from chunk start s (search for candidates from index k on):
 // emits every cut up to and including the next candidate cut and returns that
-// candidate's index, or emits the remaining forced cuts and n and returns m.
+// candidate's index, or emits the remaining forced cuts and n and returns m,
+// or (limit reached) stops and returns m.
 template <class Emit>
-__device__ uint32_t chain_next(const uint64_t *__restrict__ C, uint32_t m, uint64_t n,
+__device__ uint32_t chain_next(const uint64_t *__restrict__ C, uint32_t m, uint64_t n, uint64_t L,
                                uint64_t mn, uint64_t mx, uint64_t s, uint32_t k, Emit emit) {
     while (s < n) {
         const uint32_t j = lower_bound_from(C, m, k, s + mn);
@@ -69,6 +75,7 @@ __device__ uint32_t chain_next(const uint64_t *__restrict__ C, uint32_t m, uint6
             emit(__ldg(C + j));
             return j;
         }
+        if (s + mx > L && L < n) return m;                 // undecided until more is known
         if (s + mx < n) {
             s += mx;                                       // forced cut
             emit(s);
@@ -83,39 +90,45 @@ __device__ uint32_t chain_next(const uint64_t *__restrict__ C, uint32_t m, uint6
 
 template <class Emit>
 __device__ __forceinline__ uint32_t step_from(const uint64_t *__restrict__ C, uint32_t m, uint64_t n,
-                                              uint64_t mn, uint64_t mx, uint32_t node, Emit emit) {
-    return chain_next(C, m, n, mn, mx, __ldg(C + node), node + 1, emit);
+                                              uint64_t L, uint64_t mn, uint64_t mx, uint32_t node,
+                                              Emit emit) {
+    return chain_next(C, m, n, L, mn, mx, __ldg(C + node), node + 1, emit);
 }
 
 // The whole chain of a stream by one thread (used for streams with few candidates).
 template <class Emit>
 __device__ void select_thread(const uint64_t *__restrict__ C, uint32_t m, uint64_t s0, uint64_t n,
                               uint64_t mn, uint64_t mx, Emit emit) {
-    uint32_t cur = chain_next(C, m, n, mn, mx, s0, 0, emit);
-    while (cur != m) cur = step_from(C, m, n, mn, mx, cur, emit);
+    const uint64_t L = ~0ull;
+    uint32_t cur = chain_next(C, m, n, L, mn, mx, s0, 0, emit);
+    while (cur != m) cur = step_from(C, m, n, L, mn, mx, cur, emit);
 }
 
 // Walk piece p (-1: from s0 to x[0]; j >= 0: from x[j] to x[j+1]).
 template <class Emit>
 __device__ void walk_piece(const uint64_t *__restrict__ C, uint32_t m, uint64_t s0, uint64_t n,
-                           uint64_t mn, uint64_t mx, int p, const uint32_t *x, Emit emit) {
+                           uint64_t L, uint64_t mn, uint64_t mx, int p, const uint32_t *x,
+                           Emit emit) {
     uint32_t cur, to;
     if (p < 0) {
         to = x[0];
-        cur = chain_next(C, m, n, mn, mx, s0, 0, emit);
+        cur = chain_next(C, m, n, L, mn, mx, s0, 0, emit);
     } else {
         cur = x[p];
         to = x[p + 1];
     }
-    while (cur != to) cur = step_from(C, m, n, mn, mx, cur, emit);
+    while (cur != to) cur = step_from(C, m, n, L, mn, mx, cur, emit);
 }
 
 // Block-wide exact selection (blockDim.x == kSelThreads) of the stream [s0, n)
-// whose sorted candidate cuts are C[0..m). Writes at most cap cuts (relative to
-// s0) to ends and the total count to *d_count.
-static __device__ void select_block(const uint64_t *__restrict__ C, uint32_t m, uint64_t s0, uint64_t n,
-                             uint64_t mn, uint64_t mx, uint64_t *__restrict__ ends, uint64_t cap,
-                             uint64_t *__restrict__ d_count) {
+// whose sorted candidate cuts (all known ones, up to L) are C[0..m). Writes at
+// most cap cuts (relative to s0) to ends and the count to *d_count.
+static __device__ void select_block(const uint64_t *__restrict__ C, uint32_t m, uint64_t s0,
+                                    uint64_t n, uint64_t mn, uint64_t mx,
+                                    uint64_t *__restrict__ ends, uint64_t cap,
+                                    uint64_t *__restrict__ d_count, uint64_t L = ~0ull,
+                                    uint64_t out_base = ~0ull) {
+    if (out_base == ~0ull) out_base = s0;
     __shared__ uint32_t q[kSelThreads];          // q[j+1] = meeting candidate of S_j, S_{j+1}
     __shared__ uint32_t x[kSelThreads + 1];      // x[j] = where T joins S_j
     __shared__ uint64_t warp_tot[kSelThreads / 32];
@@ -128,15 +141,15 @@ static __device__ void select_block(const uint64_t *__restrict__ C, uint32_t m, 
     if (p >= -1 && p < nseg) {
         uint32_t a, b;
         if (p < 0) {
-            a = chain_next(C, m, n, mn, mx, s0, 0, NoEmit{});
+            a = chain_next(C, m, n, L, mn, mx, s0, 0, NoEmit{});
             b = nseg > 0 ? 0 : m;
         } else {
             a = (uint32_t)p * K;
             b = (p + 1 < nseg) ? (uint32_t)(p + 1) * K : m;
         }
         while (a != b) {
-            if (a < b) a = step_from(C, m, n, mn, mx, a, NoEmit{});
-            else b = step_from(C, m, n, mn, mx, b, NoEmit{});
+            if (a < b) a = step_from(C, m, n, L, mn, mx, a, NoEmit{});
+            else b = step_from(C, m, n, L, mn, mx, b, NoEmit{});
         }
         q[t] = a;
     }
@@ -153,7 +166,7 @@ static __device__ void select_block(const uint64_t *__restrict__ C, uint32_t m, 
     __syncthreads();
     // phase 3: count cuts per piece
     uint64_t c = 0;
-    if (n > s0 && p >= -1 && p < nseg) walk_piece(C, m, s0, n, mn, mx, p, x, CountEmit{&c});
+    if (n > s0 && p >= -1 && p < nseg) walk_piece(C, m, s0, n, L, mn, mx, p, x, CountEmit{&c});
     // phase 4: exclusive scan of counts over the block
     uint64_t v = c;
 #pragma unroll
@@ -178,7 +191,7 @@ static __device__ void select_block(const uint64_t *__restrict__ C, uint32_t m, 
     // phase 5: write
     if (n > s0 && p >= -1 && p < nseg && c) {
         uint64_t idx = excl;
-        walk_piece(C, m, s0, n, mn, mx, p, x, WriteEmit{ends, cap, &idx, s0});
+        walk_piece(C, m, s0, n, L, mn, mx, p, x, WriteEmit{ends, cap, &idx, out_base});
     }
 }
 
@@ -195,21 +208,25 @@ __device__ __forceinline__ uint64_t first_bit_thread(const uint32_t *__restrict_
     return UINT64_MAX;
 }
 
-// Greedy selection of the stream [s0, n) by one thread from the bitmap.
+// Greedy selection of the stream [s0, n) by one thread from the bitmap (bits
+// known up to window end L - 1); returns the last cut emitted (s0 if none).
 template <class Emit>
-__device__ void select_thread_bitmap(const uint32_t *__restrict__ bitmap, uint64_t s0, uint64_t n,
-                                     uint64_t mn, uint64_t mx, Emit emit) {
+__device__ uint64_t select_thread_bitmap(const uint32_t *__restrict__ bitmap, uint64_t s0,
+                                         uint64_t n, uint64_t mn, uint64_t mx, Emit emit,
+                                         uint64_t L = ~0ull) {
     uint64_t s = s0;
     while (s < n) {
-        const uint64_t lo = s + mn, hi = min(s + mx, n);
+        const uint64_t lo = s + mn, hi = min(min(s + mx, n), L);
         uint64_t cut;
         const uint64_t p = lo <= hi ? first_bit_thread(bitmap, lo - 1, hi - 1) : UINT64_MAX;
         if (p != UINT64_MAX) cut = p + 1;
+        else if (s + mx > L && L < n) break;               // undecided until more is known
         else if (s + mx < n) cut = s + mx;
         else cut = n;
         emit(cut);
         s = cut;
     }
+    return s;
 }
 
 }  // namespace hg

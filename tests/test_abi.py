@@ -59,3 +59,16 @@ def test_init_without_gpu_fails_cleanly():
     h = C.c_void_p()
     assert _lib.lib.hg_init(C.byref(h), 0, 0) == _lib.HG_ECUDA
     assert h.value is None
+
+
+def test_cdc_hash_plan_is_host_only():
+    import paper_1202_3669_b300 as hgb
+    assert hgb.cdc_hash_plan(0) == []
+    for n in (1, 8192, (16 << 20) + 1, 64 << 20, 67100231, 1 << 30, 5 << 30):
+        b = hgb.cdc_hash_plan(n)
+        assert b[0] == 0 and b[-1] == n and all(x < y for x, y in zip(b, b[1:]))
+        assert all(x % 8192 == 0 for x in b[:-1]) and len(b) - 1 <= 64
+        if n <= (64 << 20):
+            assert b == [0, n]                          # small buffers: one pass
+        else:
+            assert all(y - x >= (16 << 20) for x, y in zip(b, b[1:]))

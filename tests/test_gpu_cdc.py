@@ -152,3 +152,42 @@ def test_config_cdc_two_versions(hg, versions):
         out.append((ends, dg))
     frac = oracle.shared_fraction(out[0][0], out[0][1], out[1][0], out[1][1])
     assert 0.3 < frac < 0.99
+
+
+@pytest.mark.parametrize("n", [0, 1, 5000, 3 << 20, (20 << 20) + 12345, (100 << 20) + 7])
+@pytest.mark.parametrize("algo", [oracle.MD5, oracle.SHA1])
+def test_cdc_hash_pipelined(hg, n, algo):
+    """hg_cdc_hash (segmented, digests as chunks are decided) equals the oracle."""
+    data = G.uniform_bytes(n, seed=n + 7)
+    d = to_device(data, 0 if n % 2 else 5)
+    ends, cnt, dg = hg.cdc_hash(d, algo)
+    hg.sync()
+    k = int(cnt.item())
+    want = oracle.cdc(data, nthreads=8)
+    assert np.array_equal(ends[:k].cpu().numpy().astype(np.uint64), want)
+    assert np.array_equal(dg[:k].cpu().numpy(), oracle.hash_chunks(algo, data, want))
+
+
+def test_cdc_hash_dense_and_params(hg):
+    """Candidate-list overflow (bitmap walk with a limit) and other parameters, segmented."""
+    import paper_1202_3669_b300 as hgb
+    data = G.uniform_bytes((97 << 20) + 99, seed=77)
+    for p in (hgb.params(mask_bits=3, magic=1, min_chunk=256, max_chunk=4096),
+              hgb.params(window=17, mask_bits=9, magic=0x55, min_chunk=700, max_chunk=70000)):
+        ends, cnt, dg = hg.cdc_hash(to_device(data), hgb.MD5, p)
+        hg.sync()
+        k = int(cnt.item())
+        want = oracle.select(oracle.window_candidates(data, p.window, p.mask_bits, p.magic, nthreads=8),
+                             data.size, p.min_chunk, p.max_chunk)
+        assert np.array_equal(ends[:k].cpu().numpy().astype(np.uint64), want)
+        assert np.array_equal(dg[:k].cpu().numpy(), oracle.hash_chunks(oracle.MD5, data, want))
+
+
+def test_config_cdc_two_versions_pipelined(hg, versions):
+    for v in versions:
+        ends, cnt, dg = hg.cdc_hash(to_device(v), oracle.MD5)
+        hg.sync()
+        k = int(cnt.item())
+        want = oracle.cdc(v, nthreads=16)
+        assert np.array_equal(ends[:k].cpu().numpy().astype(np.uint64), want)
+        assert np.array_equal(dg[:k].cpu().numpy(), oracle.hash_chunks(oracle.MD5, v, want))
