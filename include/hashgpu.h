@@ -174,6 +174,21 @@ int hg_hash_chunks(hg_ctx *ctx, int algo, const uint8_t *d_in, uint64_t n, const
 int hg_cdc_hash(hg_ctx *ctx, int algo, const uint8_t *d_in, uint64_t n, const hg_cdc_params *params,
                 uint64_t *d_ends, uint64_t cap, uint64_t *d_count, uint8_t *d_digests,
                 void *stream);
+/*
+ * hg_cdc_hash on input that is still in host memory: the call itself copies
+ * h_in (n bytes, pinned for an asynchronous copy, Sec. 3.1 "One-copy host to
+ * device data transfers") into the device buffer d_in in pieces of 8 MiB and
+ * up, on a context copy stream, and each piece's window hashing starts as
+ * soon as it has landed, so the copy overlaps the hashing (Sec. 3.2.3,
+ * overlapping the transfer of one block with the computation on another).
+ * The copies of all contexts on a device share one copy stream, so calls made
+ * on several streams transfer one after the other rather than interleaved.
+ * d_in keeps the bytes afterwards. Other arguments as hg_cdc_hash (launched
+ * directly rather than from a graph).
+ */
+int hg_cdc_hash_h2d(hg_ctx *ctx, int algo, const uint8_t *h_in, uint8_t *d_in, uint64_t n,
+                    const hg_cdc_params *params, uint64_t *d_ends, uint64_t cap,
+                    uint64_t *d_count, uint8_t *d_digests, void *stream);
 /* The segment schedule hg_cdc_hash uses for n bytes: returns the number of
  * segments S (0 for n = 0) and writes up to max of the S + 1 bounds (0 ...
  * n) when bounds is not NULL. Each segment enqueues five kernels. */

@@ -21,7 +21,7 @@ from ._lib import (HG_MD5, HG_SHA1, HashGPUError, check, default_params,  # noqa
                    HG_REQ_BLOCKS, HG_REQ_CDC, hg_cancel, hg_poll, hg_release, hg_request, hg_result,
                    hg_server_config, hg_server_create, hg_server_default_config, hg_server_destroy,
                    hg_server_get_stats, hg_server_replay, hg_server_stats, hg_server_wait_any,
-                   hg_submit, hg_cdc_hash, hg_cdc_hash_plan)
+                   hg_submit, hg_cdc_hash, hg_cdc_hash_plan, hg_cdc_hash_h2d)
 
 MD5, SHA1 = HG_MD5, HG_SHA1
 DIGEST_LEN = {MD5: 16, SHA1: 20}
@@ -153,6 +153,23 @@ class Context:
         ends, count, dg = out
         check(hg_cdc_hash(self.h, algo, _ptr(data), n, p, _ptr(ends), ends.numel(), _ptr(count),
                           _ptr(dg), _stream(stream)), "hg_cdc_hash")
+        return ends, count, dg
+
+    def cdc_hash_from_host(self, host: torch.Tensor, dev: torch.Tensor, algo: int = MD5,
+                           p: hg_cdc_params | None = None, out=None, stream=None):
+        """hg_cdc_hash_h2d: copy the (pinned) host bytes into dev in pieces, overlapped with
+        the chunking. Returns (ends, count, digests)."""
+        p = p or default_params()
+        n = host.numel()
+        assert dev.numel() >= n
+        cap = n // p.min_chunk + 2
+        if out is None:
+            out = (torch.empty(cap, dtype=torch.int64, device=self.device),
+                   torch.zeros(1, dtype=torch.int64, device=self.device),
+                   torch.empty((cap, DIGEST_LEN[algo]), dtype=torch.uint8, device=self.device))
+        ends, count, dg = out
+        check(hg_cdc_hash_h2d(self.h, algo, _ptr(host), _ptr(dev), n, p, _ptr(ends), ends.numel(),
+                              _ptr(count), _ptr(dg), _stream(stream)), "hg_cdc_hash_h2d")
         return ends, count, dg
 
     def cdc(self, data: torch.Tensor, algo: int = MD5, p: hg_cdc_params | None = None,

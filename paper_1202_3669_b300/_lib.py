@@ -74,6 +74,7 @@ SIGNATURES = {
     "hg_hash_chunks": (_i32, [_vp, _i32, _vp, _u64, _vp, _u64, _vp, _vp, _vp]),
     "hg_cdc_hash": (_i32, [_vp, _i32, _vp, _u64, C.POINTER(hg_cdc_params), _vp, _u64, _vp, _vp, _vp]),
     "hg_cdc_hash_plan": (_u32, [_u64, _vp, _u32]),
+    "hg_cdc_hash_h2d": (_i32, [_vp, _i32, _vp, _vp, _u64, C.POINTER(hg_cdc_params), _vp, _u64, _vp, _vp, _vp]),
     "hg_batch_create": (_i32, [_vp, _vp, _u32, C.POINTER(hg_cdc_params), C.POINTER(_vp)]),
     "hg_batch_destroy": (_i32, [_vp]),
     "hg_batch_slots": (_u64, [_vp, _vp]),
@@ -278,3 +279,8 @@ def hg_cdc_hash(ctx, algo, d_in, n, params, d_ends, cap, d_count, d_digests, str
 
 def hg_cdc_hash_plan(n, bounds_ptr, max_n) -> int:
     return lib.hg_cdc_hash_plan(n, bounds_ptr, max_n)
+
+
+def hg_cdc_hash_h2d(ctx, algo, h_in, d_in, n, params, d_ends, cap, d_count, d_digests, stream) -> int:
+    return lib.hg_cdc_hash_h2d(ctx, algo, h_in, d_in, n, C.byref(params), d_ends, cap, d_count,
+                               d_digests, stream)

@@ -380,7 +380,9 @@ int launch_compact(const uint32_t *d_bitmap, uint64_t n, const uint32_t *d_tile_
 int launch_pipe_segment(const uint8_t *d_in, uint64_t n, const hg_cdc_params &p, int algo,
                         uint32_t tile0, uint32_t ntiles, uint64_t L, int seg, uint64_t max_chunks,
                         const PipeBufs &b, cudaStream_t s_win, cudaStream_t s_sel,
-                        cudaStream_t s_hash, cudaEvent_t ev_win, cudaEvent_t ev_sel) {
+                        cudaStream_t s_hash, cudaEvent_t ev_win, cudaEvent_t ev_sel,
+                        cudaEvent_t ev_input) {
+    if (ev_input) cudaStreamWaitEvent(s_win, ev_input, 0);    // this segment's bytes are in place
     // windows run back to back on s_win; the small serial steps (scan, compaction,
     // selection) of segment k run on s_sel, in segment order, once its windows are done
     int r;

@@ -26,6 +26,8 @@ struct hg_ctx {
     cudaEvent_t p_ev_win[64] = {}, p_ev_sel[64] = {};
     void *d_pipe = nullptr;
     cudaStream_t p_cap = nullptr;           // capture origin of the pipeline graph
+    cudaStream_t p_copy = nullptr;          // host -> device segment copies (hg_cdc_hash_h2d)
+    cudaEvent_t p_ev_copy[64] = {};
     cudaGraphExec_t p_exec = nullptr;       // replayed while p_key matches
     uint64_t p_key[16] = {};
     uint64_t scratch_gen = 0;               // bumped whenever scratch is reallocated
@@ -97,7 +99,8 @@ int launch_window_range(const uint8_t *d_in, uint64_t n, const hg_cdc_params &p,
 int launch_pipe_segment(const uint8_t *d_in, uint64_t n, const hg_cdc_params &p, int algo,
                         uint32_t tile0, uint32_t ntiles, uint64_t L, int seg, uint64_t max_chunks,
                         const PipeBufs &b, cudaStream_t s_win, cudaStream_t s_sel,
-                        cudaStream_t s_hash, cudaEvent_t ev_win, cudaEvent_t ev_sel);
+                        cudaStream_t s_hash, cudaEvent_t ev_win, cudaEvent_t ev_sel,
+                        cudaEvent_t ev_input);
 int launch_scan_tiles(const uint32_t *d_tile_cnt, uint64_t ntiles, uint64_t *d_tile_off,
                       uint64_t *d_total, cudaStream_t s);
 int launch_select(const uint64_t *d_cands, const uint64_t *d_ncand, uint64_t cand_cap,

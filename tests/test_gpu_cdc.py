@@ -191,3 +191,18 @@ def test_config_cdc_two_versions_pipelined(hg, versions):
         want = oracle.cdc(v, nthreads=16)
         assert np.array_equal(ends[:k].cpu().numpy().astype(np.uint64), want)
         assert np.array_equal(dg[:k].cpu().numpy(), oracle.hash_chunks(oracle.MD5, v, want))
+
+
+@pytest.mark.parametrize("n", [5000, (20 << 20) + 3, (70 << 20) + 11])
+def test_cdc_hash_from_host(hg, n):
+    """hg_cdc_hash_h2d: the call copies pinned host bytes in pieces while it chunks."""
+    data = G.uniform_bytes(n, seed=n + 1)
+    host = torch.from_numpy(data).pin_memory()
+    dev = torch.empty(n, dtype=torch.uint8, device="cuda")
+    ends, cnt, dg = hg.cdc_hash_from_host(host, dev, oracle.SHA1)
+    hg.sync()
+    k = int(cnt.item())
+    want = oracle.cdc(data, nthreads=8)
+    assert np.array_equal(ends[:k].cpu().numpy().astype(np.uint64), want)
+    assert np.array_equal(dg[:k].cpu().numpy(), oracle.hash_chunks(oracle.SHA1, data, want))
+    assert torch.equal(dev.cpu(), host)
