@@ -123,6 +123,23 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ helpers -------------------
+def max_over_ranks(times_ms, world, device=None):
+    """Per-step times of this rank -> the maximum over all ranks (replicas run the same
+    workload, so the slowest rank sets the job's time). No-op on one rank."""
+    if world <= 1:
+        return [float(t) for t in times_ms]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(times_ms, dtype=torch.float64,
+                     device=device if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
+def replica_throughput(bytes_per_rank, world, step_ms):
+    """Whole-job GB/s: every rank hashes bytes_per_rank per step (weak scaling)."""
+    return world * bytes_per_rank / (step_ms / 1e3) / 1e9
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -423,13 +440,9 @@ def main():
         extras["cpu_baseline"] = cpu_baseline(versions)
 
     # max over ranks
-    t_dev_all, t_e2e_all = t_dev, t_e2e
-    if world > 1:
-        t = torch.tensor([t_dev, t_e2e], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_dev_all, t_e2e_all = float(t[0]), float(t[1])
+    t_dev_all, t_e2e_all = max_over_ranks([t_dev, t_e2e], world, dev)
     if rank == 0:
-        value = world * nbytes / (t_dev_all / 1e3) / 1e9
+        value = replica_throughput(nbytes, world, t_dev_all)
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_dev_all,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
@@ -441,7 +454,7 @@ def main():
                           "chunks": [k0, k1], "shared_fraction": shared,
                           "l2": "flushed between steps (256 MiB memset)",
                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-               "e2e": {"value": world * nbytes / (t_e2e_all / 1e3) / 1e9, "unit": UNIT,
+               "e2e": {"value": replica_throughput(nbytes, world, t_e2e_all), "unit": UNIT,
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                        "pinned_h2d_copy_GBps": h2d_gbps},
                "gpu_launches": launches_per_step * args.steps,

@@ -195,6 +195,32 @@ int hg_cdc_hash_h2d(hg_ctx *ctx, int algo, const uint8_t *h_in, uint8_t *d_in, u
 uint32_t hg_cdc_hash_plan(uint64_t n, uint64_t *bounds, uint32_t max);
 
 /*
+ * Streaming chunking (Sec. 3.2.4, "Content-based Chunking Integration"): a
+ * stream written in buffers of any size is chunked buffer by buffer; when a
+ * chunk boundary does not line up with the end of a buffer, the leftover
+ * bytes (the still-open chunk) are carried into the next buffer. The stream
+ * keeps that chunk plus the window - 1 bytes before it in its own device
+ * working buffers, so the caller's buffer may be reused once the call's work
+ * has run. Each feed writes the chunks the data seen so far decides: their
+ * ends as offsets in the whole stream, their digests, and their number in
+ * *d_count (device); close writes the rest. Over the whole stream the results
+ * equal hg_cdc_hash on the concatenated bytes.
+ * max_feed_bytes bounds len per feed (HG_ECAPACITY above it); cap (entries
+ * of d_ends, rows of d_digests) must be >= (max_feed_bytes + max_chunk +
+ * window) / min_chunk + 2, or >= (carried + len) / min_chunk + 1 for that
+ * feed. A feed waits on the host for the previous feed's work to finish (to
+ * learn how many bytes it carried), then enqueues its own on `stream`.
+ */
+typedef struct hg_cdc_stream hg_cdc_stream;
+int hg_stream_open(hg_ctx *ctx, int algo, const hg_cdc_params *params, uint64_t max_feed_bytes,
+                   hg_cdc_stream **out);
+int hg_stream_feed(hg_cdc_stream *st, const uint8_t *d_data, uint64_t len, uint64_t *d_ends,
+                   uint64_t cap, uint64_t *d_count, uint8_t *d_digests, void *stream);
+int hg_stream_close(hg_cdc_stream *st, uint64_t *d_ends, uint64_t cap, uint64_t *d_count,
+                    uint8_t *d_digests, void *stream);
+int hg_stream_destroy(hg_cdc_stream *st);
+
+/*
  * Batched chunking and chunk digests for many files in one pass (Sec. 3.2.3:
  * the runtime batches a stream of hashing jobs; Sec. 4.1: the gains need
  * batches; Sec. 3.2.4: writes are buffered so one GPU job covers many chunks).

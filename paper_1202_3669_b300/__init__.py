@@ -21,7 +21,8 @@ from ._lib import (HG_MD5, HG_SHA1, HashGPUError, check, default_params,  # noqa
                    HG_REQ_BLOCKS, HG_REQ_CDC, hg_cancel, hg_poll, hg_release, hg_request, hg_result,
                    hg_server_config, hg_server_create, hg_server_default_config, hg_server_destroy,
                    hg_server_get_stats, hg_server_replay, hg_server_stats, hg_server_wait_any,
-                   hg_submit, hg_cdc_hash, hg_cdc_hash_plan, hg_cdc_hash_h2d)
+                   hg_submit, hg_cdc_hash, hg_cdc_hash_plan, hg_cdc_hash_h2d, hg_stream_open,
+                   hg_stream_feed, hg_stream_close, hg_stream_destroy)
 
 MD5, SHA1 = HG_MD5, HG_SHA1
 DIGEST_LEN = {MD5: 16, SHA1: 20}
@@ -353,5 +354,46 @@ class Server:
     def __del__(self):
         try:
             self.close()
+        except Exception:
+            pass
+
+
+class CdcStream:
+    """Chunk a stream fed in device buffers of any size (hg_stream_*); results in stream offsets."""
+
+    def __init__(self, ctx: Context, algo: int = MD5, p: hg_cdc_params | None = None,
+                 max_feed: int = 64 << 20):
+        self.ctx, self.algo = ctx, algo
+        self.p = p or default_params()
+        self.max_feed = max_feed
+        self.h = hg_stream_open(ctx.h, algo, self.p, max_feed)
+        self.cap = (max_feed + self.p.max_chunk + self.p.window) // self.p.min_chunk + 2
+        dev = ctx.device
+        self._ends = torch.empty(self.cap, dtype=torch.int64, device=dev)
+        self._cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+        self._dg = torch.empty((self.cap, DIGEST_LEN[algo]), dtype=torch.uint8, device=dev)
+
+    def _take(self):
+        k = int(self._cnt.item())
+        return self._ends[:k].clone(), self._dg[:k].clone()
+
+    def feed(self, data: torch.Tensor, stream=None):
+        """Feed bytes; returns (ends, digests) of the chunks this feed decided."""
+        check(hg_stream_feed(self.h, _ptr(data), data.numel(), _ptr(self._ends), self.cap,
+                             _ptr(self._cnt), _ptr(self._dg), _stream(stream)), "hg_stream_feed")
+        return self._take()
+
+    def close(self, stream=None):
+        check(hg_stream_close(self.h, _ptr(self._ends), self.cap, _ptr(self._cnt), _ptr(self._dg),
+                              _stream(stream)), "hg_stream_close")
+        out = self._take()
+        hg_stream_destroy(self.h)
+        self.h = None
+        return out
+
+    def __del__(self):
+        try:
+            if self.h:
+                hg_stream_destroy(self.h)
         except Exception:
             pass

@@ -75,6 +75,10 @@ SIGNATURES = {
     "hg_cdc_hash": (_i32, [_vp, _i32, _vp, _u64, C.POINTER(hg_cdc_params), _vp, _u64, _vp, _vp, _vp]),
     "hg_cdc_hash_plan": (_u32, [_u64, _vp, _u32]),
     "hg_cdc_hash_h2d": (_i32, [_vp, _i32, _vp, _vp, _u64, C.POINTER(hg_cdc_params), _vp, _u64, _vp, _vp, _vp]),
+    "hg_stream_open": (_i32, [_vp, _i32, C.POINTER(hg_cdc_params), _u64, C.POINTER(_vp)]),
+    "hg_stream_feed": (_i32, [_vp, _vp, _u64, _vp, _u64, _vp, _vp, _vp]),
+    "hg_stream_close": (_i32, [_vp, _vp, _u64, _vp, _vp, _vp]),
+    "hg_stream_destroy": (_i32, [_vp]),
     "hg_batch_create": (_i32, [_vp, _vp, _u32, C.POINTER(hg_cdc_params), C.POINTER(_vp)]),
     "hg_batch_destroy": (_i32, [_vp]),
     "hg_batch_slots": (_u64, [_vp, _vp]),
@@ -284,3 +288,21 @@ def hg_cdc_hash_plan(n, bounds_ptr, max_n) -> int:
 def hg_cdc_hash_h2d(ctx, algo, h_in, d_in, n, params, d_ends, cap, d_count, d_digests, stream) -> int:
     return lib.hg_cdc_hash_h2d(ctx, algo, h_in, d_in, n, C.byref(params), d_ends, cap, d_count,
                                d_digests, stream)
+
+
+def hg_stream_open(ctx, algo, params, max_feed) -> int:
+    h = _vp()
+    check(lib.hg_stream_open(ctx, algo, C.byref(params), max_feed, C.byref(h)), "hg_stream_open")
+    return h.value
+
+
+def hg_stream_feed(st, d_data, n, d_ends, cap, d_count, d_digests, stream) -> int:
+    return lib.hg_stream_feed(st, d_data, n, d_ends, cap, d_count, d_digests, stream)
+
+
+def hg_stream_close(st, d_ends, cap, d_count, d_digests, stream) -> int:
+    return lib.hg_stream_close(st, d_ends, cap, d_count, d_digests, stream)
+
+
+def hg_stream_destroy(st) -> int:
+    return lib.hg_stream_destroy(st)

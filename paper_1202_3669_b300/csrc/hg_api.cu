@@ -361,7 +361,7 @@ static int enqueue_cdc_hash(hg_ctx *c, int algo, const uint8_t *d_in, uint64_t n
         const uint32_t nt = (uint32_t)((hi + kWinTile - 1) / kWinTile - t0);
         const uint64_t L = (k == nseg - 1) ? n : hi;
         const uint64_t max_chunks = (hi - lo + p->max_chunk) / p->min_chunk + 2;
-        if ((r = launch_pipe_segment(d_in, n, *p, algo, t0, nt, L, k, max_chunks, pb, c->p_win,
+        if ((r = launch_pipe_segment(d_in, n, n, *p, algo, t0, nt, L, k, max_chunks, pb, c->p_win,
                                      c->p_sel, c->p_hash[k], c->p_ev_win[k], c->p_ev_sel[k],
                                      h_in ? c->p_ev_copy[k] : nullptr)))
             return r;

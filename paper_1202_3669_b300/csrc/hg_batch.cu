@@ -93,8 +93,10 @@ int hg_batch_create(hg_ctx *ctx, const uint64_t *h_file_off, uint32_t nfile,
     if (rc == HG_OK) {
         b->win_max_per_sm = job_window_occupancy(p->window);
         b->tune.window_ctas_per_sm = b->win_max_per_sm;
-        b->tune.hash_threads = 128;
-        b->tune.hash_ctas_per_sm = 8;
+        // one warp per scheduler: a SHA-1 warp alone saturates its scheduler's
+        // ALU pipe, so long chains run fastest without neighbours
+        b->tune.hash_threads = 32;
+        b->tune.hash_ctas_per_sm = 4;
         b->tune.long_chunk_bytes = 16384;
     }
     cudaSetDevice(prev);
@@ -232,8 +234,8 @@ int hg_batch_autotune(hg_batch *b, int algo, const uint8_t *d_data, uint64_t *d_
         if (ms < best_ms) { best_ms = ms; top = cur; }
     }
     if (rc == HG_OK) {
-        for (int ht : {64, 128, 256})
-            for (int hc : {4, 8, 16})
+        for (int ht : {32, 64, 128})
+            for (int hc : {2, 4, 8})
                 for (uint64_t lb : {8192ull, 32768ull}) {
                     cur = top;
                     cur.hash_threads = ht;

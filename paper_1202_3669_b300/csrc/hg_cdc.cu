@@ -311,10 +311,49 @@ __global__ void __launch_bounds__(128) k_hash_seg(const uint8_t *__restrict__ in
     const uint64_t lo = st->seg_cnt[seg], hi = st->seg_cnt[seg + 1];
     const uint64_t i = lo + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= hi) return;
-    const uint64_t a = i ? ends[i - 1] : 0, b = ends[i];
+    const uint64_t a = i ? ends[i - 1] : st->start0, b = ends[i];
     H hs;
     hash_range(in + a, b - a, hs);
     store_digest(hs, out + i * H::kDigest);
+}
+
+// Streaming: start a feed whose first chunk starts at start0 of the buffer.
+__global__ void k_stream_init(PipeState *st, uint64_t start0) {
+    if (threadIdx.x == 0) {
+        st->carry = start0;
+        st->start0 = start0;
+        st->count = 0;
+        st->ncand = 0;
+        st->seg_cnt[0] = 0;
+    }
+}
+
+// Streaming: the feed's chunk ends, shifted to stream offsets, and its count.
+__global__ void k_stream_out(const uint64_t *__restrict__ ends, const PipeState *st, uint64_t base,
+                             uint64_t *__restrict__ out, uint64_t cap, uint64_t *count_out) {
+    const uint64_t cnt = st->count;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt && i < cap;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        out[i] = ends[i] + base;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *count_out = cnt;
+}
+
+// Streaming: copy the open chunk and the halo before it, [carry - h, wl), to the
+// start of the next working buffer; info = {carry, h, bytes copied, count}.
+__global__ void k_stream_carry(const uint8_t *__restrict__ src, uint64_t wl, const PipeState *st,
+                               uint32_t halo, uint8_t *__restrict__ dst, uint64_t *info) {
+    const uint64_t carry = st->carry;
+    const uint64_t h = carry < halo ? carry : halo;
+    const uint64_t from = carry - h, len = wl > from ? wl - from : 0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        dst[i] = src[from + i];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        info[0] = carry;
+        info[1] = h;
+        info[2] = len;
+        info[3] = st->count;
+    }
 }
 
 // Selection of the whole stream by one CTA (parallel, exact); when the
@@ -377,11 +416,28 @@ int launch_compact(const uint32_t *d_bitmap, uint64_t n, const uint32_t *d_tile_
     return cuda_status(cudaGetLastError());
 }
 
-int launch_pipe_segment(const uint8_t *d_in, uint64_t n, const hg_cdc_params &p, int algo,
-                        uint32_t tile0, uint32_t ntiles, uint64_t L, int seg, uint64_t max_chunks,
-                        const PipeBufs &b, cudaStream_t s_win, cudaStream_t s_sel,
-                        cudaStream_t s_hash, cudaEvent_t ev_win, cudaEvent_t ev_sel,
-                        cudaEvent_t ev_input) {
+int launch_stream_init(PipeState *st, uint64_t start0, cudaStream_t s) {
+    k_stream_init<<<1, 32, 0, s>>>(st, start0);
+    return cuda_status(cudaGetLastError());
+}
+
+int launch_stream_out(const uint64_t *ends, const PipeState *st, uint64_t base, uint64_t *d_ends_out,
+                      uint64_t cap, uint64_t *d_count_out, cudaStream_t s) {
+    k_stream_out<<<64, 256, 0, s>>>(ends, st, base, d_ends_out, cap, d_count_out);
+    return cuda_status(cudaGetLastError());
+}
+
+int launch_stream_carry(const uint8_t *src, uint64_t wl, const PipeState *st, uint32_t halo,
+                        uint8_t *dst, uint64_t *info, cudaStream_t s) {
+    k_stream_carry<<<64, 256, 0, s>>>(src, wl, st, halo, dst, info);
+    return cuda_status(cudaGetLastError());
+}
+
+int launch_pipe_segment(const uint8_t *d_in, uint64_t n, uint64_t n_sel, const hg_cdc_params &p,
+                        int algo, uint32_t tile0, uint32_t ntiles, uint64_t L, int seg,
+                        uint64_t max_chunks, const PipeBufs &b, cudaStream_t s_win,
+                        cudaStream_t s_sel, cudaStream_t s_hash, cudaEvent_t ev_win,
+                        cudaEvent_t ev_sel, cudaEvent_t ev_input) {
     if (ev_input) cudaStreamWaitEvent(s_win, ev_input, 0);    // this segment's bytes are in place
     // windows run back to back on s_win; the small serial steps (scan, compaction,
     // selection) of segment k run on s_sel, in segment order, once its windows are done
@@ -394,7 +450,7 @@ int launch_pipe_segment(const uint8_t *d_in, uint64_t n, const hg_cdc_params &p,
                                              &b.st->ncand);
     k_compact<<<ntiles, kWinThreads, 0, s_sel>>>(b.bitmap, (n + 31) / 32, b.tile_cnt, b.tile_off,
                                                  b.cands, b.cand_cap, tile0);
-    k_select_seg<<<1, kSelThreads, 0, s_sel>>>(b.cands, b.cand_cap, b.bitmap, n, L, p.min_chunk,
+    k_select_seg<<<1, kSelThreads, 0, s_sel>>>(b.cands, b.cand_cap, b.bitmap, n_sel, L, p.min_chunk,
                                                p.max_chunk, b.ends, b.cap, b.st, seg);
     cudaEventRecord(ev_sel, s_sel);
     cudaStreamWaitEvent(s_hash, ev_sel, 0);

@@ -75,7 +75,7 @@ struct PipeState {
     uint64_t carry;      // start of the chunk still open after the last segment
     uint64_t count;      // chunks finalized so far
     uint64_t ncand;      // candidates found so far
-    uint64_t pad;
+    uint64_t start0;     // start of the first chunk (0 for a whole buffer)
     uint64_t seg_cnt[kMaxSeg + 1];   // chunks finalized after segment k-1 (seg_cnt[0] = 0)
 };
 struct PipeBufs {
@@ -96,11 +96,19 @@ int launch_compact(const uint32_t *d_bitmap, uint64_t n, const uint32_t *d_tile_
 int launch_window_range(const uint8_t *d_in, uint64_t n, const hg_cdc_params &p,
                         uint32_t *d_bitmap, uint32_t *d_tile_cnt, uint32_t tile0, uint64_t ntiles,
                         cudaStream_t s, int *d_err);
-int launch_pipe_segment(const uint8_t *d_in, uint64_t n, const hg_cdc_params &p, int algo,
-                        uint32_t tile0, uint32_t ntiles, uint64_t L, int seg, uint64_t max_chunks,
-                        const PipeBufs &b, cudaStream_t s_win, cudaStream_t s_sel,
-                        cudaStream_t s_hash, cudaEvent_t ev_win, cudaEvent_t ev_sel,
-                        cudaEvent_t ev_input);
+// n: bytes in d_in; n_sel: end of the stream for selection (n, or ~0 when the
+// stream continues beyond d_in).
+int launch_pipe_segment(const uint8_t *d_in, uint64_t n, uint64_t n_sel, const hg_cdc_params &p,
+                        int algo, uint32_t tile0, uint32_t ntiles, uint64_t L, int seg,
+                        uint64_t max_chunks, const PipeBufs &b, cudaStream_t s_win,
+                        cudaStream_t s_sel, cudaStream_t s_hash, cudaEvent_t ev_win,
+                        cudaEvent_t ev_sel, cudaEvent_t ev_input);
+// streaming chunking (hg_stream.cu helpers in hg_cdc.cu)
+int launch_stream_init(PipeState *st, uint64_t start0, cudaStream_t s);
+int launch_stream_out(const uint64_t *ends, const PipeState *st, uint64_t base, uint64_t *d_ends_out,
+                      uint64_t cap, uint64_t *d_count_out, cudaStream_t s);
+int launch_stream_carry(const uint8_t *src, uint64_t wl, const PipeState *st, uint32_t halo,
+                        uint8_t *dst, uint64_t *info, cudaStream_t s);
 int launch_scan_tiles(const uint32_t *d_tile_cnt, uint64_t ntiles, uint64_t *d_tile_off,
                       uint64_t *d_total, cudaStream_t s);
 int launch_select(const uint64_t *d_cands, const uint64_t *d_ncand, uint64_t cand_cap,

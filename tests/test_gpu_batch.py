@@ -103,7 +103,7 @@ def test_batch_autotune_keeps_results(hg):
     d = to_device(data)
     o1 = b.cdc_hash(d, hgb.SHA1)
     best = b.autotune(d, hgb.SHA1)
-    assert best.hash_threads in (64, 128, 256) and best.window_ctas_per_sm >= 1
+    assert best.hash_threads in (32, 64, 128) and best.window_ctas_per_sm >= 1
     o2 = b.cdc_hash(d, hgb.SHA1)
     b.sync()
     assert torch.equal(o1[1], o2[1])

@@ -206,3 +206,55 @@ def test_cdc_hash_from_host(hg, n):
     assert np.array_equal(ends[:k].cpu().numpy().astype(np.uint64), want)
     assert np.array_equal(dg[:k].cpu().numpy(), oracle.hash_chunks(oracle.SHA1, data, want))
     assert torch.equal(dev.cpu(), host)
+
+
+@pytest.mark.parametrize("pieces", [
+    [1, 19, 20, 21, 5000, 65536, 65537, 1 << 20],
+    [4096] * 300,
+    [3 << 20, 7, (5 << 20) + 1],
+    [64 << 20],
+])
+@pytest.mark.parametrize("algo", [oracle.MD5, oracle.SHA1])
+def test_stream_feeds_equal_one_shot(hg, pieces, algo):
+    """Streaming with carried leftovers (Sec. 3.2.4) equals chunking the whole stream."""
+    import paper_1202_3669_b300 as hgb
+    total = sum(pieces)
+    data = G.uniform_bytes(total, seed=len(pieces) + total % 1000)
+    d = to_device(data)
+    st = hgb.CdcStream(hg, algo, max_feed=max(pieces))
+    ends, dgs, off = [], [], 0
+    for k in pieces:
+        e, g = st.feed(d[off:off + k])
+        ends.append(e.cpu().numpy())
+        dgs.append(g.cpu().numpy())
+        off += k
+    e, g = st.close()
+    ends.append(e.cpu().numpy())
+    dgs.append(g.cpu().numpy())
+    hg.sync()
+    got_e = np.concatenate(ends).astype(np.uint64)
+    got_d = np.concatenate(dgs)
+    want = oracle.cdc(data, nthreads=8)
+    assert np.array_equal(got_e, want)
+    assert np.array_equal(got_d, oracle.hash_chunks(algo, data, want))
+
+
+def test_stream_other_params_and_tiny_min(hg):
+    import paper_1202_3669_b300 as hgb
+    p = hgb.params(window=17, mask_bits=6, magic=0x11, min_chunk=8, max_chunk=3000)
+    data = G.uniform_bytes(400_000, seed=5)
+    d = to_device(data)
+    st = hgb.CdcStream(hg, hgb.MD5, p, max_feed=50_000)
+    ends, off = [], 0
+    for k in [1, 2, 3, 16, 17, 18, 50_000, 49_999, 30_000] + [25_000] * 10:
+        if off >= data.size:
+            break
+        k = min(k, data.size - off)
+        ends.append(st.feed(d[off:off + k])[0].cpu().numpy())
+        off += k
+    if off < data.size:
+        ends.append(st.feed(d[off:])[0].cpu().numpy())
+    ends.append(st.close()[0].cpu().numpy())
+    got = np.concatenate(ends).astype(np.uint64)
+    want = oracle.select(oracle.window_candidates(data, 17, 6, 0x11, nthreads=8), data.size, 8, 3000)
+    assert np.array_equal(got, want)
