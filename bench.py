@@ -167,12 +167,19 @@ def cpu_baseline(versions, budget_s: float = 12.0):
     import oracle
     nthreads = os.cpu_count() or 1
     L = oracle.lib()
-    # calibrate on 256 KiB, then size the sample to about budget_s seconds
-    probe = versions[0][: 256 << 10]
-    t0 = time.perf_counter()
-    e = oracle.cdc(probe, nthreads=nthreads, L=L)
-    oracle.hash_chunks(oracle.MD5, probe, e, L=L)
-    rate = probe.size / max(1e-6, time.perf_counter() - t0)
+    # calibrate on growing prefixes (thread start-up dominates tiny probes), then size the
+    # sample to about budget_s seconds; the whole workload is the upper bound
+    probe_n, rate = 1 << 20, 0.0
+    while True:
+        probe = versions[0][:probe_n]
+        t0 = time.perf_counter()
+        e = oracle.cdc(probe, nthreads=nthreads, L=L)
+        oracle.hash_chunks(oracle.MD5, probe, e, L=L)
+        dt = time.perf_counter() - t0
+        rate = probe.size / max(1e-6, dt)
+        if dt >= 0.5 or probe_n >= versions[0].size:
+            break
+        probe_n = min(versions[0].size, probe_n * 4)
     nbytes = int(min(versions[0].size, max(1 << 20, rate * budget_s / 2)))
     total, t0 = 0, time.perf_counter()
     for v in versions:
