@@ -37,6 +37,8 @@ def _bind(L: C.CDLL) -> C.CDLL:
     L.hgo_digest.restype = C.c_int
     L.hgo_hash_blocks.argtypes = [C.c_int, u8p, C.c_uint64, C.c_uint64, u8p, u8p]
     L.hgo_hash_blocks.restype = C.c_int64
+    L.hgo_hash_blocks_pmd.argtypes = [C.c_int, u8p, C.c_uint64, C.c_uint64, C.c_uint64, u8p]
+    L.hgo_hash_blocks_pmd.restype = C.c_int64
     L.hgo_window_hash.argtypes = [u8p, C.c_uint32]
     L.hgo_window_hash.restype = C.c_uint32
     L.hgo_window_candidates.argtypes = [u8p, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32,
@@ -86,6 +88,18 @@ def hash_blocks(algo: int, data, block: int, root: bool = True, L=None):
     got = L.hgo_hash_blocks(algo, _ptr(a), a.size, block, _ptr(dg), rt.ctypes.data if root else None)
     assert got == nblk
     return dg, (rt.tobytes() if root else None)
+
+
+def hash_blocks_pmd(algo: int, data, block: int, segment: int, L=None):
+    """Two-level block identifiers, uint8[nblk, dlen]."""
+    L = L or lib()
+    a = _u8(data)
+    dl = DIGEST_LEN[algo]
+    nblk = (a.size + block - 1) // block
+    ids = np.zeros((max(nblk, 1), dl), np.uint8)
+    got = L.hgo_hash_blocks_pmd(algo, _ptr(a), a.size, block, segment, _ptr(ids))
+    assert got == nblk
+    return ids[:nblk]
 
 
 def window_hash(win, L=None) -> int:

@@ -41,6 +41,34 @@ int64_t hgo_hash_blocks(int algo, const uint8_t *in, uint64_t n, uint64_t block,
     return (int64_t)nblk;
 }
 
+/*
+ * Two-level (parallel Merkle-Damgard) block identifiers, Sec. 3.2.2 "Direct
+ * Hashing": inside each block the segments are hashed independently and the
+ * block's identifier is the hash of its segment digests in order. Written out
+ * block by block, segment by segment, as the definition reads.
+ */
+int64_t hgo_hash_blocks_pmd(int algo, const uint8_t *in, uint64_t n, uint64_t block,
+                            uint64_t segment, uint8_t *ids) {
+    int dl = hgo_digest_len(algo);
+    if (dl == 0 || block == 0 || segment == 0 || block % segment != 0) return -1;
+    uint64_t nblk = (n + block - 1) / block;
+    uint8_t *buf = malloc((block / segment) * (uint64_t)dl + 1);
+    if (!buf) return -1;
+    for (uint64_t i = 0; i < nblk; i++) {
+        uint64_t lo = i * block;
+        uint64_t blk_end = lo + block < n ? lo + block : n;
+        uint64_t nseg = 0;
+        for (uint64_t a = lo; a < blk_end; a += segment) {
+            uint64_t b = a + segment < blk_end ? a + segment : blk_end;
+            hgo_digest(algo, in + a, b - a, buf + nseg * (uint64_t)dl);
+            nseg++;
+        }
+        hgo_digest(algo, buf, nseg * (uint64_t)dl, ids + i * (uint64_t)dl);
+    }
+    free(buf);
+    return (int64_t)nblk;
+}
+
 int hgo_hash_chunks(int algo, const uint8_t *in, const uint64_t *ends,
                     uint64_t nchunk, uint8_t *digests) {
     int dl = hgo_digest_len(algo);

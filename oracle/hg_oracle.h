@@ -13,6 +13,9 @@
  *   hgo_md5 / hgo_sha1        -> hashlib (OpenSSL) at every length 0..2048 and
  *                                on random MiB-sized inputs
  *   hgo_hash_blocks           -> hashlib per block and over the digest list
+ *   hgo_hash_blocks_pmd       -> hashlib per segment and over each block's
+ *                                segment digests; reduces to H(H(block)) when
+ *                                segment == block
  *   hgo_window_hash/_candidates -> hashlib.md5 of every window (brute force)
  *   hgo_select                -> hand-worked fixtures in tests/golden and a
  *                                checker of the properties that determine the
@@ -47,6 +50,17 @@ int hgo_digest(int algo, const uint8_t *msg, uint64_t len, uint8_t *out);
  */
 int64_t hgo_hash_blocks(int algo, const uint8_t *in, uint64_t n, uint64_t block,
                         uint8_t *digests, uint8_t *root);
+
+/*
+ * Two-level block identifiers (Sec. 3.2.2 "Direct Hashing", the parallel
+ * Merkle-Damgard construction): block i = [i*block, min((i+1)*block, n)) is
+ * cut into segments of `segment` bytes (the last one may be short), each
+ * segment is digested, and ids[i] = digest of the block's segment digests in
+ * order. block must be a multiple of segment. Returns the number of blocks,
+ * or -1 on bad arguments.
+ */
+int64_t hgo_hash_blocks_pmd(int algo, const uint8_t *in, uint64_t n, uint64_t block,
+                            uint64_t segment, uint8_t *ids);
 
 /*
  * Sliding-window hash (Sec. 2.1 "Content-based chunking", Sec. 3.2.2): the

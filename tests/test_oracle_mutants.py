@@ -36,6 +36,12 @@ MUTANTS = [
                  "hgo_digest(algo, digests, (nblk ? nblk - 1 : 0) * (uint64_t)dl, root);"),
     ("direct.c", "uint64_t hi = lo + block < n ? lo + block : n;",
                  "uint64_t hi = lo + block;"),                          # pads the short block
+    ("direct.c", "uint64_t b = a + segment < blk_end ? a + segment : blk_end;",
+                 "uint64_t b = a + segment;"),                          # pads the short segment
+    ("direct.c", "hgo_digest(algo, buf, nseg * (uint64_t)dl, ids + i * (uint64_t)dl);",
+                 "hgo_digest(algo, buf, (nseg - 1) * (uint64_t)dl, ids + i * (uint64_t)dl);"),
+    ("direct.c", "for (uint64_t a = lo; a < blk_end; a += segment) {",
+                 "for (uint64_t a = 0; a < blk_end - lo; a += segment) {"),  # segments from 0
     ("cdc.c", "j->cuts[j->count++] = p + 1;", "j->cuts[j->count++] = p;"),  # cut before window
     ("cdc.c", "return (uint32_t)d[0] | ((uint32_t)d[1] << 8)", "return (uint32_t)d[3] | ((uint32_t)d[2] << 8)"),
     ("cdc.c", "cands[k] < s + min_chunk", "cands[k] <= s + min_chunk"),  # exclusive min
@@ -75,6 +81,14 @@ def pins_pass(L) -> bool:
         dg, root = oracle.hash_blocks(algo, data, 1024, L=L)
         parts = [ref_digest(algo, data[i:i + 1024]) for i in range(0, 5000, 1024)]
         if [r.tobytes() for r in dg] != parts or root != ref_digest(algo, b"".join(parts)):
+            return False
+        ids = oracle.hash_blocks_pmd(algo, data, 2100, 300, L=L)
+        want = []
+        for lo in range(0, 5000, 2100):
+            blk = data[lo:lo + 2100]
+            want.append(ref_digest(algo, b"".join(ref_digest(algo, blk[a:a + 300])
+                                                  for a in range(0, len(blk), 300))))
+        if [r.tobytes() for r in ids] != want:
             return False
     small = G.uniform_bytes(1500, seed=5).tobytes()
     if oracle.window_candidates(small, 20, 4, 5, L=L).tolist() != brute_window_cuts(small, 20, 4, 5):
