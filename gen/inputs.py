@@ -41,7 +41,9 @@ def text_like_bytes(n: int, seed: int, line: int = 80, zipf_s: float = 1.1) -> n
 
     Symbols are i.i.d. from a finite Zipf(s) law over the 95 printable ASCII
     characters (rank k has probability proportional to k^-s); rank k maps to a
-    character through a seeded permutation. The stream is cut to n bytes.
+    character through a seeded permutation. A symbol is drawn by inverting the
+    law's CDF at a uniform 16-bit level (probabilities quantised to 2^-16, so
+    a GiB takes seconds). The stream is cut to n bytes.
     """
     g = rng(seed)
     chars = np.arange(32, 127, dtype=np.uint8)          # 95 printable
@@ -49,14 +51,16 @@ def text_like_bytes(n: int, seed: int, line: int = 80, zipf_s: float = 1.1) -> n
     w = np.arange(1, 96, dtype=np.float64) ** (-zipf_s)
     cdf = np.cumsum(w / w.sum())
     cdf[-1] = 1.0
+    levels = (np.arange(1 << 16, dtype=np.float64) + 0.5) / (1 << 16)
+    table = perm[np.searchsorted(cdf, levels, side="right").clip(0, 94)]   # 16-bit level -> char
     nlines = (n + line - 1) // line
     out = np.empty(nlines * line, dtype=np.uint8)
     view = out.reshape(nlines, line)
     step = max(1, (64 * MiB) // line)
     for r0 in range(0, nlines, step):
         r1 = min(nlines, r0 + step)
-        u = g.random((r1 - r0, line - 1))
-        view[r0:r1, : line - 1] = perm[np.searchsorted(cdf, u, side="right").clip(0, 94)]
+        u = g.integers(0, 1 << 16, size=(r1 - r0, line - 1), dtype=np.uint16)
+        view[r0:r1, : line - 1] = table[u]
     view[:, line - 1] = ord("\n")
     return out[:n].copy()
 

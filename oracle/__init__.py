@@ -44,6 +44,11 @@ def _bind(L: C.CDLL) -> C.CDLL:
     L.hgo_window_candidates.argtypes = [u8p, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32,
                                         u64p, C.c_uint64, C.c_int]
     L.hgo_window_candidates.restype = C.c_uint64
+    L.hgo_rabin_fingerprint.argtypes = [u8p, C.c_uint64]
+    L.hgo_rabin_fingerprint.restype = C.c_uint32
+    L.hgo_window_candidates_kind.argtypes = [u8p, C.c_uint64, C.c_int, C.c_uint32, C.c_uint32,
+                                             C.c_uint32, u64p, C.c_uint64, C.c_int]
+    L.hgo_window_candidates_kind.restype = C.c_uint64
     L.hgo_select.argtypes = [u64p, C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint64, u64p, C.c_uint64]
     L.hgo_select.restype = C.c_uint64
     L.hgo_hash_chunks.argtypes = [C.c_int, u8p, u64p, C.c_uint64, u8p]
@@ -108,16 +113,35 @@ def window_hash(win, L=None) -> int:
     return int(L.hgo_window_hash(_ptr(a), a.size))
 
 
+WIN_MD5, WIN_RABIN = 0, 1
+RABIN_POLY = 0x9E3779BB
+
+
+def rabin_fingerprint(msg, L=None) -> int:
+    L = L or lib()
+    a = _u8(msg)
+    return int(L.hgo_rabin_fingerprint(_ptr(a), a.size))
+
+
 def window_candidates(data, window: int = 20, mask_bits: int = 13, magic: int = 0x0F0F,
-                      nthreads: int = 1, L=None) -> np.ndarray:
-    """Sorted candidate cut positions (uint64)."""
+                      nthreads: int = 1, L=None, kind: int = WIN_MD5) -> np.ndarray:
+    """Sorted candidate cut positions (uint64); kind picks the MD5 or the Rabin window."""
     L = L or lib()
     a = _u8(data)
-    cnt = L.hgo_window_candidates(_ptr(a), a.size, window, mask_bits, magic, None, 0, nthreads)
+    if kind == WIN_MD5:
+        cnt = L.hgo_window_candidates(_ptr(a), a.size, window, mask_bits, magic, None, 0, nthreads)
+    else:
+        cnt = L.hgo_window_candidates_kind(_ptr(a), a.size, kind, window, mask_bits, magic, None,
+                                           0, nthreads)
+    assert cnt != 2 ** 64 - 1, kind
     out = np.zeros(cnt, np.uint64)
     if cnt:
-        got = L.hgo_window_candidates(_ptr(a), a.size, window, mask_bits, magic,
-                                      _ptr(out), cnt, nthreads)
+        if kind == WIN_MD5:
+            got = L.hgo_window_candidates(_ptr(a), a.size, window, mask_bits, magic,
+                                          _ptr(out), cnt, nthreads)
+        else:
+            got = L.hgo_window_candidates_kind(_ptr(a), a.size, kind, window, mask_bits, magic,
+                                               _ptr(out), cnt, nthreads)
         assert got == cnt
     return out
 
@@ -143,10 +167,11 @@ def hash_chunks(algo: int, data, ends, L=None) -> np.ndarray:
 
 
 def cdc(data, window: int = 20, mask_bits: int = 13, magic: int = 0x0F0F,
-        min_chunk: int = 2048, max_chunk: int = 65536, nthreads: int = 1, L=None) -> np.ndarray:
+        min_chunk: int = 2048, max_chunk: int = 65536, nthreads: int = 1, L=None,
+        kind: int = WIN_MD5) -> np.ndarray:
     """Chunk ends of the whole content-defined chunking step."""
     a = _u8(data)
-    c = window_candidates(a, window, mask_bits, magic, nthreads, L)
+    c = window_candidates(a, window, mask_bits, magic, nthreads, L, kind)
     return select(c, a.size, min_chunk, max_chunk, L)
 
 

@@ -4,7 +4,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["md5.c", "sha1.c", "direct.c", "cdc.c"]
+SOURCES = ["md5.c", "sha1.c", "direct.c", "cdc.c", "rabin.c"]
 LIB = os.path.join(HERE, "liboracle.so")
 
 

@@ -31,15 +31,18 @@ uint32_t hgo_window_hash(const uint8_t *win, uint32_t window) {
     return (uint32_t)d[0] | ((uint32_t)d[1] << 8) | ((uint32_t)d[2] << 16) | ((uint32_t)d[3] << 24);
 }
 
-static int is_candidate(const uint8_t *in, uint64_t p, uint32_t window,
+static int is_candidate(const uint8_t *in, uint64_t p, int kind, uint32_t window,
                         uint32_t mask, uint32_t magic) {
-    uint32_t h = hgo_window_hash(in + p + 1 - window, window);
+    const uint8_t *w = in + p + 1 - window;
+    uint32_t h = kind == HGO_WIN_RABIN ? hgo_rabin_fingerprint(w, window)
+                                       : hgo_window_hash(w, window);
     return (h & mask) == magic;
 }
 
 typedef struct {
     const uint8_t *in;
     uint64_t p_lo, p_hi;          /* window end positions [p_lo, p_hi) */
+    int kind;
     uint32_t window, mask, magic;
     uint64_t *cuts, count, cap;
 } range_job;
@@ -47,7 +50,7 @@ typedef struct {
 static void *scan_range(void *arg) {
     range_job *j = (range_job *)arg;
     for (uint64_t p = j->p_lo; p < j->p_hi; p++) {
-        if (is_candidate(j->in, p, j->window, j->mask, j->magic)) {
+        if (is_candidate(j->in, p, j->kind, j->window, j->mask, j->magic)) {
             if (j->count == j->cap) {             /* grow the private list */
                 uint64_t nc = j->cap ? 2 * j->cap : 1024;
                 uint64_t *nb = (uint64_t *)realloc(j->cuts, nc * sizeof(uint64_t));
@@ -63,6 +66,14 @@ static void *scan_range(void *arg) {
 uint64_t hgo_window_candidates(const uint8_t *in, uint64_t n, uint32_t window,
                                uint32_t mask_bits, uint32_t magic,
                                uint64_t *cuts, uint64_t cap, int nthreads) {
+    return hgo_window_candidates_kind(in, n, HGO_WIN_MD5, window, mask_bits, magic, cuts, cap,
+                                      nthreads);
+}
+
+uint64_t hgo_window_candidates_kind(const uint8_t *in, uint64_t n, int kind, uint32_t window,
+                                    uint32_t mask_bits, uint32_t magic,
+                                    uint64_t *cuts, uint64_t cap, int nthreads) {
+    if (kind != HGO_WIN_MD5 && kind != HGO_WIN_RABIN) return UINT64_MAX;
     if (window == 0 || n < window) return 0;
     uint32_t mask = mask_bits >= 32 ? 0xffffffffu : ((1u << mask_bits) - 1u);
     uint64_t first = window - 1, npos = n - first;
@@ -74,6 +85,7 @@ uint64_t hgo_window_candidates(const uint8_t *in, uint64_t n, uint32_t window,
         jobs[t].in = in;
         jobs[t].p_lo = first + npos * (uint64_t)t / (uint64_t)nthreads;
         jobs[t].p_hi = first + npos * (uint64_t)(t + 1) / (uint64_t)nthreads;
+        jobs[t].kind = kind;
         jobs[t].window = window; jobs[t].mask = mask; jobs[t].magic = magic;
     }
     if (nthreads == 1) scan_range(&jobs[0]);

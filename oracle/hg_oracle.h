@@ -17,6 +17,11 @@
  *                                segment digests; reduces to H(H(block)) when
  *                                segment == block
  *   hgo_window_hash/_candidates -> hashlib.md5 of every window (brute force)
+ *   hgo_rabin_fingerprint     -> GF(2) facts: P irreducible (Ben-Or test),
+ *                                low-degree strings are their own remainder,
+ *                                x^31 leaves P - x^31, linearity in the bits,
+ *                                x^(2^31 - 1) = 1 (P primitive, 2^31 - 1 prime),
+ *                                and the one-byte shift identity
  *   hgo_select                -> hand-worked fixtures in tests/golden and a
  *                                checker of the properties that determine the
  *                                greedy chunking uniquely
@@ -32,6 +37,10 @@ extern "C" {
 #endif
 
 enum { HGO_MD5 = 0, HGO_SHA1 = 1 };
+/* window hash kinds: the paper's MD5 window, or a Rabin fingerprint window */
+enum { HGO_WIN_MD5 = 0, HGO_WIN_RABIN = 1 };
+/* the degree-31 irreducible polynomial of the Rabin window (bit k = x^k) */
+#define HGO_RABIN_POLY 0x9E3779BBu
 
 /* RFC 1321: MD5 of len bytes; 16-byte digest in the standard byte order. */
 void hgo_md5(const uint8_t *msg, uint64_t len, uint8_t out[16]);
@@ -67,6 +76,22 @@ int64_t hgo_hash_blocks_pmd(int algo, const uint8_t *in, uint64_t n, uint64_t bl
  * first four MD5 digest bytes, read little-endian, of the `window` bytes at win.
  */
 uint32_t hgo_window_hash(const uint8_t *win, uint32_t window);
+
+/*
+ * Rabin fingerprint (variant window hash, LBFS-style; see rabin.c): the
+ * remainder modulo HGO_RABIN_POLY of the polynomial of the len bytes at msg,
+ * read as one big-endian binary number. A 31-bit value.
+ */
+uint32_t hgo_rabin_fingerprint(const uint8_t *msg, uint64_t len);
+
+/*
+ * As hgo_window_candidates, with the window hash chosen by kind: HGO_WIN_MD5
+ * (hgo_window_hash) or HGO_WIN_RABIN (hgo_rabin_fingerprint of the window).
+ * Returns the total count, or UINT64_MAX for an unknown kind.
+ */
+uint64_t hgo_window_candidates_kind(const uint8_t *in, uint64_t n, int kind, uint32_t window,
+                                    uint32_t mask_bits, uint32_t magic,
+                                    uint64_t *cuts, uint64_t cap, int nthreads);
 
 /*
  * Boundary candidates: every cut position c = p + 1, p in [window-1, n-1],

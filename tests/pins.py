@@ -26,6 +26,13 @@ def brute_window_cuts(data: bytes, window: int, mask_bits: int, magic: int) -> l
     return out
 
 
+def brute_window_cuts_with(data: bytes, window: int, mask_bits: int, magic: int, fp) -> list[int]:
+    """Cut position p+1 of every window ending at p whose hash fp(window bytes) low bits match."""
+    mask = (1 << mask_bits) - 1 if mask_bits < 32 else 0xFFFFFFFF
+    return [p + 1 for p in range(window - 1, len(data))
+            if fp(data[p - window + 1:p + 1]) & mask == magic]
+
+
 def check_chunking(ends, cands, n: int, mn: int, mx: int) -> None:
     """Assert that `ends` is the one chunking the min/max greedy rule admits.
 

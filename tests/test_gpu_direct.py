@@ -69,6 +69,17 @@ def test_config_1gib_uniform(hg, gib_uniform, algo, block):
     hg.sync()
 
 
+@pytest.mark.parametrize("algo", ALGOS)
+def test_config_1gib_text_like(hg, algo):
+    """1 GiB text-like (seed 5), 64 KiB blocks + hash-of-hashes."""
+    data = G.text_like_bytes(1 << 30, seed=5)
+    dg, root = hg.hash_blocks(to_device(data), 65536, algo)
+    odg, oroot = oracle.hash_blocks(algo, data, 65536)
+    assert np.array_equal(dg.cpu().numpy(), odg)
+    assert root.cpu().numpy().tobytes() == oroot
+    hg.sync()
+
+
 def test_bad_arguments(hg):
     import paper_1202_3669_b300 as hgb
     d = to_device(G.uniform_bytes(100, 1))
@@ -77,4 +88,58 @@ def test_bad_arguments(hg):
     out = torch.empty(64, dtype=torch.uint8, device="cuda")
     with pytest.raises(hgb.HashGPUError):
         hg.hash_blocks(d, 64, hgb.MD5, out=out[1:33])       # misaligned digests
+    hg.sync()
+
+
+# ---------------------------------------------------------------- two-level identifiers
+PMD_SMALL = [(0, 4096, 1024), (1, 4096, 1024), (4095, 4096, 1024), (4097, 4096, 1024),
+             (1_000_003, 65536, 4096), (3 << 20, 1 << 20, 4096), (100_000, 700, 100),
+             (70_000, 128, 64), (64, 64, 64), (200_000, 8192, 8192)]
+
+
+@pytest.mark.parametrize("algo", ALGOS)
+@pytest.mark.parametrize("n,block,segment", PMD_SMALL)
+@pytest.mark.parametrize("offset", [0, 5])
+def test_two_level_small(hg, algo, n, block, segment, offset):
+    data = G.uniform_bytes(n, seed=n + block + segment)
+    d = to_device(data, offset)
+    ids = hg.hash_blocks_pmd(d, block, segment, algo)
+    torch.cuda.synchronize()
+    hg.sync()
+    assert np.array_equal(ids.cpu().numpy(), oracle.hash_blocks_pmd(algo, data, block, segment))
+
+
+@pytest.mark.parametrize("algo", ALGOS)
+@pytest.mark.parametrize("block,segment", [(1 << 20, 4096), (65536, 4096)])
+def test_two_level_1gib(hg, gib_uniform, algo, block, segment):
+    d = to_device(gib_uniform)
+    dl = 16 if algo == oracle.MD5 else 20
+    seg = torch.empty(((1 << 30) // segment, dl), dtype=torch.uint8, device="cuda")
+    ids = hg.hash_blocks_pmd(d, block, segment, algo, seg_out=seg)
+    got = ids.cpu().numpy()
+    # the segment digests are the plain fixed-block digests at the segment size
+    sdg, _ = oracle.hash_blocks(algo, gib_uniform, segment, root=False)
+    assert np.array_equal(seg.cpu().numpy(), sdg)
+    want = oracle.hash_blocks_pmd(algo, gib_uniform, block, segment)
+    assert np.array_equal(got, want)
+    hg.sync()
+
+
+def test_two_level_text_like(hg):
+    data = G.text_like_bytes(5_000_017, seed=5)
+    ids = hg.hash_blocks_pmd(to_device(data, 3), 1 << 20, 4096, oracle.SHA1)
+    assert np.array_equal(ids.cpu().numpy(), oracle.hash_blocks_pmd(oracle.SHA1, data, 1 << 20, 4096))
+    hg.sync()
+
+
+def test_two_level_bad_arguments(hg):
+    import paper_1202_3669_b300 as hgb
+    d = to_device(G.uniform_bytes(10_000, 1))
+    with pytest.raises(hgb.HashGPUError):
+        hg.hash_blocks_pmd(d, 4096, 1000, hgb.MD5)           # block not a multiple of segment
+    with pytest.raises(hgb.HashGPUError):
+        hg.hash_blocks_pmd(d, 4096, 0, hgb.MD5)              # zero segment
+    seg = torch.empty(64 * 16 + 8, dtype=torch.uint8, device="cuda")
+    with pytest.raises(hgb.HashGPUError):
+        hg.hash_blocks_pmd(d, 4096, 1024, hgb.MD5, seg_out=seg[4:])   # misaligned segment digests
     hg.sync()

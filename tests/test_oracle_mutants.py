@@ -15,7 +15,7 @@ import pytest
 
 import oracle
 from gen import inputs as G
-from tests.pins import brute_window_cuts, check_chunking, ref_digest
+from tests.pins import brute_window_cuts, brute_window_cuts_with, check_chunking, ref_digest
 
 ORACLE_DIR = os.path.dirname(os.path.abspath(oracle.__file__))
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -42,6 +42,13 @@ MUTANTS = [
                  "hgo_digest(algo, buf, (nseg - 1) * (uint64_t)dl, ids + i * (uint64_t)dl);"),
     ("direct.c", "for (uint64_t a = lo; a < blk_end; a += segment) {",
                  "for (uint64_t a = 0; a < blk_end - lo; a += segment) {"),  # segments from 0
+    ("rabin.c", "for (int j = 7; j >= 0; j--) {", "for (int j = 0; j < 8; j++) {"),   # bit order
+    ("rabin.c", "if (r & 0x80000000u) r ^= HGO_RABIN_POLY;",
+                "if (r & 0x40000000u) r ^= HGO_RABIN_POLY;"),           # wrong degree
+    ("rabin.c", "r = (r << 1) | ((msg[i] >> j) & 1u);",
+                "r = (r << 1) ^ ((msg[len - 1 - i] >> j) & 1u);"),      # bytes reversed
+    ("cdc.c", "uint32_t h = kind == HGO_WIN_RABIN ? hgo_rabin_fingerprint(w, window)",
+              "uint32_t h = kind == HGO_WIN_RABIN ? hgo_rabin_fingerprint(w + 1, window - 1)"),
     ("cdc.c", "j->cuts[j->count++] = p + 1;", "j->cuts[j->count++] = p;"),  # cut before window
     ("cdc.c", "return (uint32_t)d[0] | ((uint32_t)d[1] << 8)", "return (uint32_t)d[3] | ((uint32_t)d[2] << 8)"),
     ("cdc.c", "cands[k] < s + min_chunk", "cands[k] <= s + min_chunk"),  # exclusive min
@@ -64,7 +71,7 @@ def build_mutant(tmp_path, fname, old, new):
     out = d / "libmut.so"
     subprocess.run(["gcc", "-std=c99", "-O1", "-fPIC", "-shared", "-pthread",
                     "-D_POSIX_C_SOURCE=200809L", "-o", str(out),
-                    *[str(d / f) for f in ("md5.c", "sha1.c", "direct.c", "cdc.c")], "-lm"],
+                    *[str(d / f) for f in ("md5.c", "sha1.c", "direct.c", "cdc.c", "rabin.c")], "-lm"],
                    check=True)
     return oracle.lib(str(out))
 
@@ -90,6 +97,20 @@ def pins_pass(L) -> bool:
                                                   for a in range(0, len(blk), 300))))
         if [r.tobytes() for r in ids] != want:
             return False
+    # Rabin window: hand-reduced values and GF(2) linearity, candidates per window
+    if oracle.rabin_fingerprint(b"\x80\0\0\0", L) != 0x1E3779BB:
+        return False
+    if oracle.rabin_fingerprint(b"\x01\0\0\0\0", L) != 0x3C6EF376:
+        return False
+    if oracle.rabin_fingerprint(b"\x12\x34\x56", L) != 0x123456:
+        return False
+    a, b = G.uniform_bytes(64, 21), G.uniform_bytes(64, 22)
+    if oracle.rabin_fingerprint(a ^ b, L) != oracle.rabin_fingerprint(a, L) ^ oracle.rabin_fingerprint(b, L):
+        return False
+    small_r = G.uniform_bytes(1200, seed=23).tobytes()
+    if oracle.window_candidates(small_r, 24, 3, 2, L=L, kind=oracle.WIN_RABIN).tolist() != \
+            brute_window_cuts_with(small_r, 24, 3, 2, lambda w: oracle.rabin_fingerprint(w, L)):
+        return False
     small = G.uniform_bytes(1500, seed=5).tobytes()
     if oracle.window_candidates(small, 20, 4, 5, L=L).tolist() != brute_window_cuts(small, 20, 4, 5):
         return False
