@@ -17,7 +17,8 @@ the chunking; the D2H of counts, boundaries + digests is inside the timed
 region too.
 The line also carries the roofline of the dominant kernel (the window-hash
 kernel), the CPU oracle baseline, the fixed-block direct-hashing throughputs
-(1 GiB, MD5/SHA-1, 4 KiB blocks) and the clocks seen while timing.
+(1 GiB, MD5/SHA-1, 4 KiB / 64 KiB / 1 MiB blocks, two-level identifiers) and the clocks
+seen while timing.
 
 --impl reference times the CPU oracle on the host cores on bounded samples of
 the same workload (there is no reference implementation to install).
@@ -480,35 +481,47 @@ def main():
 
 
 def direct_leg(hgb, ctx, dev, flush):
-    """Fixed-block MD5 / SHA-1 over 1 GiB of uniform bytes, 4 KiB blocks (digests only, and
-    digests + hash-of-hashes), kernel time with CUDA events, L2 flushed between launches."""
+    """Fixed-block MD5 / SHA-1 over 1 GiB of uniform bytes at 4 KiB, 64 KiB and 1 MiB blocks
+    (digests only; at 4 KiB also digests + hash-of-hashes), and two-level identifiers of
+    1 MiB blocks over 4 KiB segments; kernel time with CUDA events, L2 flushed between
+    launches."""
     import torch
     from gen import inputs as G
     data = torch.from_numpy(G.uniform_bytes(1 << 30, seed=4)).to(dev)
     res = {}
     peaks, kind = measured_peaks()
     s = torch.cuda.current_stream(dev)
+
+    def timed(fn, reps=8, warm=3):
+        ts = []
+        for i in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            fn()
+            b.record(s)
+            if i >= warm:
+                ts.append((a, b))
+        torch.cuda.synchronize()
+        t = sum(a.elapsed_time(b) for a, b in ts) / len(ts) / 1e3
+        return {"GBps": (1 << 30) / t / 1e9, "ms": t * 1e3,
+                "hbm_frac": (1 << 30) / t / 1e9 / peaks["hbm_gbs"]}
+
     for algo, name in ((hgb.MD5, "md5"), (hgb.SHA1, "sha1")):
         dl = 16 if algo == hgb.MD5 else 20
         out = torch.empty(((1 << 30) // 4096, dl), dtype=torch.uint8, device=dev)
         rt = torch.empty(dl, dtype=torch.uint8, device=dev)
-        for root in (False, True):
-            ts = []
-            for i in range(8):
-                flush.zero_()
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(s)
-                ctx.hash_blocks(data, 4096, algo, root=root, out=out, root_out=rt)
-                b.record(s)
-                if i >= 3:
-                    ts.append((a, b))
-            torch.cuda.synchronize()
-            t = sum(a.elapsed_time(b) for a, b in ts) / len(ts) / 1e3
-            key = f"{name}_4KiB" + ("_with_root" if root else "")
-            res[key] = {"GBps": (1 << 30) / t / 1e9, "ms": t * 1e3,
-                        "hbm_frac": (1 << 30) / t / 1e9 / peaks["hbm_gbs"]}
+        for block, label in ((4096, "4KiB"), (65536, "64KiB"), (1 << 20, "1MiB")):
+            res[f"{name}_{label}"] = timed(
+                lambda: ctx.hash_blocks(data, block, algo, root=False, out=out))
+        res[f"{name}_4KiB_with_root"] = timed(
+            lambda: ctx.hash_blocks(data, 4096, algo, root=True, out=out, root_out=rt), reps=5, warm=2)
+        ids = torch.empty(((1 << 30) >> 20, dl), dtype=torch.uint8, device=dev)
+        res[f"{name}_1MiB_two_level_4KiB"] = timed(
+            lambda: ctx.hash_blocks_pmd(data, 1 << 20, 4096, algo, out=ids, seg_out=out))
     ctx.sync()
-    res["note"] = f"1 GiB uniform bytes (seed 4), 262144 blocks; HBM peak {peaks['hbm_gbs']} GB/s ({kind})"
+    res["note"] = (f"1 GiB uniform bytes (seed 4); 262144 / 16384 / 1024 blocks; two-level = "
+                   f"H(4 KiB segment digests) per 1 MiB block; HBM peak {peaks['hbm_gbs']} GB/s ({kind})")
     return res
 
 

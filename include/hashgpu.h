@@ -118,6 +118,22 @@ int hg_hash_blocks(hg_ctx *ctx, int algo, const uint8_t *d_in, uint64_t n, uint6
                    uint8_t *d_digests, uint8_t *d_root, void *stream);
 
 /*
+ * Two-level block identifiers, the parallel Merkle-Damgard construction of
+ * Sec. 3.2.2 "Direct Hashing": block i = [i*block, min((i+1)*block, n)) is cut
+ * into segments of `segment` bytes (the last may be short), every segment is
+ * digested independently, and d_ids[i] = H(segment digests of block i, in
+ * order) with the same algo. This is a different identifier from the plain
+ * digest of the block (hg_hash_blocks): it removes the block-long serial chain.
+ * block must be a multiple of segment (HG_EINVAL otherwise).
+ * d_seg_digests: ceil(n/segment)*dlen bytes, 16-byte aligned, receives the
+ * segment digests; NULL keeps them in context scratch (counted against the
+ * budget, HG_ENOMEM if it does not fit). d_ids: ceil(n/block)*dlen bytes,
+ * 4-byte aligned. n = 0 writes nothing.
+ */
+int hg_hash_blocks_pmd(hg_ctx *ctx, int algo, const uint8_t *d_in, uint64_t n, uint64_t block,
+                       uint64_t segment, uint8_t *d_seg_digests, uint8_t *d_ids, void *stream);
+
+/*
  * Sliding-window hashing, Sec. 3.2.2 "Content-based chunking": bit p of the
  * bitmap (word p/32, bit p%32) is set when the window ending at byte p is a
  * candidate (see hg_cdc_params); bits for p < window-1 and p >= n are 0.

@@ -17,7 +17,7 @@ from ._lib import (HG_MD5, HG_SHA1, HashGPUError, check, default_params,  # noqa
                    hg_batch_destroy, hg_batch_get_tuning, hg_batch_set_tuning, hg_batch_slots,
                    hg_batch_sync, hg_batch_tuning, hg_cdc_boundaries, hg_cdc_boundaries_static,
                    hg_cdc_candidates, hg_cdc_params, hg_destroy, hg_digest_len, hg_hash_blocks,
-                   hg_hash_chunks, hg_init, hg_reserve, hg_scratch_bytes, hg_sync, hg_window_bitmap,
+                   hg_hash_blocks_pmd, hg_hash_chunks, hg_init, hg_reserve, hg_scratch_bytes, hg_sync, hg_window_bitmap,
                    HG_REQ_BLOCKS, HG_REQ_CDC, hg_cancel, hg_poll, hg_release, hg_request, hg_result,
                    hg_server_config, hg_server_create, hg_server_default_config, hg_server_destroy,
                    hg_server_get_stats, hg_server_replay, hg_server_stats, hg_server_wait_any,
@@ -94,6 +94,20 @@ class Context:
         check(hg_hash_blocks(self.h, algo, _ptr(data), n, block, _ptr(out),
                              _ptr(root_out) if root else None, _stream(stream)), "hg_hash_blocks")
         return out, (root_out if root else None)
+
+    def hash_blocks_pmd(self, data: torch.Tensor, block: int, segment: int, algo: int = MD5,
+                        out: torch.Tensor | None = None, seg_out: torch.Tensor | None = None,
+                        stream=None) -> torch.Tensor:
+        """Two-level block identifiers (H of each block's segment digests)."""
+        n = data.numel()
+        nblk = (n + block - 1) // block if block > 0 else 0
+        dl = DIGEST_LEN.get(algo, 16)
+        if out is None:
+            out = torch.empty((nblk, dl), dtype=torch.uint8, device=self.device)
+        check(hg_hash_blocks_pmd(self.h, algo, _ptr(data), n, block, segment,
+                                 _ptr(seg_out) if seg_out is not None else None, _ptr(out),
+                                 _stream(stream)), "hg_hash_blocks_pmd")
+        return out
 
     def window_bitmap(self, data: torch.Tensor, p: hg_cdc_params | None = None,
                       out: torch.Tensor | None = None, stream=None) -> torch.Tensor:

@@ -68,6 +68,7 @@ SIGNATURES = {
     "hg_sync": (_i32, [_vp, _vp]),
     "hg_scratch_bytes": (_u64, [_vp]),
     "hg_hash_blocks": (_i32, [_vp, _i32, _vp, _u64, _u64, _vp, _vp, _vp]),
+    "hg_hash_blocks_pmd": (_i32, [_vp, _i32, _vp, _u64, _u64, _u64, _vp, _vp, _vp]),
     "hg_window_bitmap": (_i32, [_vp, _vp, _u64, C.POINTER(hg_cdc_params), _vp, _vp]),
     "hg_cdc_candidates": (_i32, [_vp, _vp, _u64, C.POINTER(hg_cdc_params), _vp, _u64, _vp, _vp]),
     "hg_cdc_boundaries": (_i32, [_vp, _vp, _u64, C.POINTER(hg_cdc_params), _vp, _u64, _vp, _vp]),
@@ -166,6 +167,10 @@ def hg_digest_len(algo: int) -> int:
 
 def hg_hash_blocks(ctx, algo, d_in, n, block, d_digests, d_root, stream) -> int:
     return lib.hg_hash_blocks(ctx, algo, d_in, n, block, d_digests, d_root, stream)
+
+
+def hg_hash_blocks_pmd(ctx, algo, d_in, n, block, segment, d_seg_digests, d_ids, stream) -> int:
+    return lib.hg_hash_blocks_pmd(ctx, algo, d_in, n, block, segment, d_seg_digests, d_ids, stream)
 
 
 def hg_window_bitmap(ctx, d_in, n, params, d_bitmap, stream) -> int:

@@ -139,6 +139,7 @@ int hg_destroy(hg_ctx *c) {
     cudaFree(c->d_tile_cnt);
     cudaFree(c->d_tile_off);
     cudaFree(c->d_cands);
+    cudaFree(c->d_segdig);
     cudaFree(c->d_err);
     if (c->pipe_ready) {
         if (c->p_exec) cudaGraphExecDestroy(c->p_exec);
@@ -194,6 +195,32 @@ int hg_hash_blocks(hg_ctx *c, int algo, const uint8_t *d_in, uint64_t n, uint64_
     if (r) return r;
     if (d_root) r = launch_root(algo, d_digests, nblk * (uint64_t)hg_digest_len(algo), d_root, s);
     return r;
+}
+
+int hg_hash_blocks_pmd(hg_ctx *c, int algo, const uint8_t *d_in, uint64_t n, uint64_t block,
+                       uint64_t segment, uint8_t *d_seg_digests, uint8_t *d_ids, void *stream) {
+    const int dl = hg_digest_len(algo);
+    if (!c || dl < 0 || segment == 0 || block == 0 || block % segment) return HG_EINVAL;
+    const uint64_t nblk = (n + block - 1) / block, nseg = (n + segment - 1) / segment;
+    if (nblk == 0) return HG_OK;
+    if (!d_in || !d_ids || (reinterpret_cast<uintptr_t>(d_ids) & 3) ||
+        (reinterpret_cast<uintptr_t>(d_seg_digests) & 15))
+        return HG_EINVAL;
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    int r;
+    uint8_t *seg = d_seg_digests;
+    if (!seg) {
+        if ((r = ensure(c, (void **)&c->d_segdig, &c->segdig_cap, nseg * (uint64_t)dl, 1))) return r;
+        seg = c->d_segdig;
+    }
+    // level 1: every segment of the input (blocks are whole numbers of
+    // segments, so the segment grid of the input is that of every block)
+    if ((r = launch_hash_blocks(algo, d_in, n, segment, seg, s, c->d_err))) return r;
+    // level 2: block i's identifier digests its (block/segment) segment
+    // digests, which sit contiguously; the last block may have fewer
+    return launch_hash_blocks(algo, seg, nseg * (uint64_t)dl, (block / segment) * (uint64_t)dl, d_ids,
+                              s, c->d_err);
 }
 
 int hg_window_bitmap(hg_ctx *c, const uint8_t *d_in, uint64_t n, const hg_cdc_params *p,

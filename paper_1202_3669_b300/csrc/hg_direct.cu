@@ -23,17 +23,12 @@ __global__ void __launch_bounds__(128) k_hash_blocks(const uint8_t *__restrict__
     store_digest(hs, out + i * H::kDigest);
 }
 
-// Full blocks of a 16-byte aligned input whose block size is a multiple of
+// One full block of a 16-byte aligned input whose block size is a multiple of
 // 64: four aligned 16-byte loads per MD5/SHA-1 block and the padding block as
-// constants. Capped at 32 registers so 2048 threads fit an SM: with one chain
-// per thread, occupancy is what hides the loads (measured 4.1 vs 3.3 TB/s for
-// the same loop at 37 registers).
+// constants.
 template <class H>
-__global__ void __launch_bounds__(128, 16) k_hash_blocks_aligned(const uint8_t *__restrict__ in,
-                                                                  uint64_t block, uint64_t nfull,
-                                                                  uint8_t *__restrict__ out) {
-    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nfull) return;
+__device__ __forceinline__ void hash_aligned_block(const uint8_t *__restrict__ in, uint64_t block,
+                                                   uint64_t i, uint8_t *__restrict__ out) {
     const uint4 *p = reinterpret_cast<const uint4 *>(in + i * block);
     const uint64_t nb = block >> 6;
     H hs;
@@ -48,6 +43,32 @@ __global__ void __launch_bounds__(128, 16) k_hash_blocks_aligned(const uint8_t *
     uint32_t Z[16] = {0x80u, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     H::put_length(Z, block);
     hs.compress(Z);
+    store_digest(hs, out + i * H::kDigest);
+}
+
+// Many blocks: the throughput form, capped at 32 registers so 2048 threads
+// fit an SM: with one chain per thread, occupancy is what hides the loads
+// (measured 4.1 vs 3.3 TB/s for the same loop at 37 registers).
+template <class H>
+__global__ void __launch_bounds__(128, 16) k_hash_blocks_aligned(const uint8_t *__restrict__ in,
+                                                                  uint64_t block, uint64_t nfull,
+                                                                  uint8_t *__restrict__ out) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nfull) hash_aligned_block<H>(in, block, i, out);
+}
+
+// Few blocks (fewer chains than it takes to fill the integer pipes): each
+// block is a latency-bound chain, so the chain form of the step, loads two
+// blocks ahead (hash_range) and no register cap; small CTAs spread the chains
+// over the SMs.
+template <class H>
+__global__ void __launch_bounds__(64) k_hash_blocks_aligned_few(const uint8_t *__restrict__ in,
+                                                                uint64_t block, uint64_t nfull,
+                                                                uint8_t *__restrict__ out) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nfull) return;
+    H hs;
+    hash_range(in + i * block, block, hs);
     store_digest(hs, out + i * H::kDigest);
 }
 
@@ -136,6 +157,10 @@ int launch_multi_blocks(const BlkReq *d_reqs, uint32_t nreq, uint64_t total_bloc
     return cuda_status(cudaGetLastError());
 }
 
+// Below this many chains (about 512 threads per SM) the block kernels are
+// latency-bound rather than integer-pipe-bound.
+constexpr uint64_t kFewChains = 148ull * 512;
+
 int launch_hash_blocks(int algo, const uint8_t *d_in, uint64_t n, uint64_t block,
                        uint8_t *d_digests, cudaStream_t s, int *) {
     const uint64_t nblk = (n + block - 1) / block;
@@ -144,10 +169,16 @@ int launch_hash_blocks(int algo, const uint8_t *d_in, uint64_t n, uint64_t block
     if (aligned) {
         // full blocks by the aligned kernel, a short last block (if any) by the generic one
         const uint64_t nfull = n / block;
-        if (nfull) {
+        if (nfull >= kFewChains) {
             const unsigned grid = (unsigned)((nfull + 127) / 128);
             if (algo == HG_MD5) k_hash_blocks_aligned<Md5><<<grid, 128, 0, s>>>(d_in, block, nfull, d_digests);
             else k_hash_blocks_aligned<Sha1><<<grid, 128, 0, s>>>(d_in, block, nfull, d_digests);
+        } else if (nfull) {
+            const unsigned grid = (unsigned)((nfull + 63) / 64);
+            if (algo == HG_MD5)
+                k_hash_blocks_aligned_few<Md5Chain><<<grid, 64, 0, s>>>(d_in, block, nfull, d_digests);
+            else
+                k_hash_blocks_aligned_few<Sha1><<<grid, 64, 0, s>>>(d_in, block, nfull, d_digests);
         }
         if (nfull < nblk) {
             const uint64_t lo = nfull * block;

@@ -19,6 +19,7 @@ struct hg_ctx {
     uint64_t *d_tile_off = nullptr;  uint64_t tile_off_cap = 0;
     uint64_t *d_cands = nullptr;     uint64_t cand_cap = 0;
     uint64_t *d_ncand = nullptr;     // one word
+    uint8_t *d_segdig = nullptr;     uint64_t segdig_cap = 0;   // two-level segment digests
     // pipelined chunking (hg_cdc_hash): streams, events, device state
     bool pipe_ready = false;
     cudaStream_t p_win = nullptr, p_sel = nullptr, p_hash[64] = {};
