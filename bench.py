@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the direct/batch/serve/CPU legs")
-    ap.add_argument("--leg", default=None, choices=["direct", "batch", "serve"],
+    ap.add_argument("--leg", default=None, choices=["direct", "batch", "serve", "rabin"],
                     help="run only this extra leg (for profiling) and print its result")
     ap.add_argument("--batch-files", type=int, default=4096,
                     help="batch leg: use only the first N files of the 4096-file workload")
@@ -259,6 +259,8 @@ def main():
             res = direct_leg(hgb, ctx, dev, flush)
         elif args.leg == "batch":
             res = batch_leg(hgb, ctx, dev, flush, nfiles=args.batch_files)
+        elif args.leg == "rabin":
+            res = rabin_leg(hgb, dev, flush)
         else:
             res = serve_leg(hgb, ctx, batch_leg(hgb, ctx, dev, flush)["batched_graph_GBps"])
         print(json.dumps({"leg": args.leg, "result": res}), flush=True)
@@ -443,6 +445,7 @@ def main():
     extras = {}
     if not args.no_extras and rank == 0:
         extras["direct"] = direct_leg(hgb, ctxs[0], dev, flush)
+        extras["rabin"] = rabin_leg(hgb, dev, flush)
         extras["batch"] = batch_leg(hgb, ctxs[0], dev, flush)
         extras["serve"] = serve_leg(hgb, ctxs[0], extras["batch"]["batched_graph_GBps"])
         extras["cpu_baseline"] = cpu_baseline(versions)
@@ -472,7 +475,7 @@ def main():
                "step_ms_p50": statistics.median(step_ms), "step_ms_max": max(step_ms),
                "unpipelined": {"GBps": nbytes / (t_two / 1e3) / 1e9, "ms_per_step": t_two,
                                "calls": "hg_cdc_boundaries + hg_hash_chunks"}}
-        for k in ("direct", "batch", "serve"):
+        for k in ("direct", "rabin", "batch", "serve"):
             if k in extras:
                 out[k] = extras[k]
         print(json.dumps(out), flush=True)
@@ -523,6 +526,61 @@ def direct_leg(hgb, ctx, dev, flush):
     res["note"] = (f"1 GiB uniform bytes (seed 4); 262144 / 16384 / 1024 blocks; two-level = "
                    f"H(4 KiB segment digests) per 1 MiB block; HBM peak {peaks['hbm_gbs']} GB/s ({kind})")
     return res
+
+
+def rabin_leg(hgb, dev, flush, steps=50):
+    """The chunking step of the main workload with the Rabin fingerprint window (48 bytes,
+    LBFS-style) instead of the MD5 window: whole step (both versions, two streams), the
+    window kernel alone on the base version, and the shared-chunk fraction."""
+    import torch
+    versions = workload()
+    p = hgb.params(window=48, window_hash=hgb.WIN_RABIN)
+    ctxs = [hgb.Context(dev.index or 0) for _ in versions]
+    streams = [torch.cuda.Stream(dev) for _ in versions]
+    d_in = [torch.from_numpy(v).to(dev) for v in versions]
+    cap = [v.size // p.min_chunk + 2 for v in versions]
+    outs = [(torch.empty(c, dtype=torch.int64, device=dev), torch.zeros(1, dtype=torch.int64, device=dev),
+             torch.empty((c, 16), dtype=torch.uint8, device=dev)) for c in cap]
+    main_s = torch.cuda.current_stream(dev)
+
+    def step():
+        ev0 = torch.cuda.Event()
+        ev0.record(main_s)
+        for i in range(len(versions)):
+            streams[i].wait_event(ev0)
+            ctxs[i].cdc_hash(d_in[i], hgb.MD5, p, out=outs[i], stream=streams[i])
+        for st in streams:
+            main_s.wait_stream(st)
+
+    def timed(fn, n):
+        ts = []
+        for i in range(n + 3):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(main_s)
+            fn()
+            b.record(main_s)
+            if i >= 3:
+                ts.append((a, b))
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ts) / len(ts) / 1e3
+
+    t_step = timed(step, steps)
+    bm = torch.empty((versions[0].size + 31) // 32, dtype=torch.int32, device=dev)
+    t_win = timed(lambda: ctxs[0].window_bitmap(d_in[0], p, out=bm, stream=main_s), 20)
+    for c in ctxs:
+        c.sync()
+    k0, k1 = int(outs[0][1].item()), int(outs[1][1].item())
+    s0 = {bytes(r) for r in outs[0][2][:k0].cpu().numpy()}
+    e1 = outs[1][0][:k1].cpu().numpy()
+    sz1 = np.diff(np.concatenate([[0], e1]))
+    shared = sum(int(z) for z, r in zip(sz1, outs[1][2][:k1].cpu().numpy()) if bytes(r) in s0)
+    nbytes = sum(v.size for v in versions)
+    return {"GBps": nbytes / t_step / 1e9, "ms_per_step": t_step * 1e3,
+            "window_kernel_GBps": versions[0].size / t_win / 1e9, "window_kernel_ms": t_win * 1e3,
+            "chunks": [k0, k1], "shared_fraction": shared / versions[1].size,
+            "params": {"window": 48, "mask_bits": 13, "magic": 0x0F0F, "min": 2048, "max": 65536,
+                       "window_hash": "rabin (degree-31 polynomial 0x9E3779BB)", "digest": "md5"}}
 
 
 def batch_leg(hgb, ctx, dev, flush, nfiles=4096):

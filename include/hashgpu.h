@@ -59,23 +59,38 @@ typedef enum { HG_MD5 = 0, HG_SHA1 = 1 } hg_algo;
 typedef struct hg_ctx hg_ctx;
 
 /*
+ * Window hash of content-defined chunking. HG_WIN_MD5 is the paper's (Sec.
+ * 3.2.2: MD5 of each window). HG_WIN_RABIN is a variant with no counterpart
+ * in the paper's experiments: the Rabin fingerprint used by LBFS, the
+ * chunking system Sec. 2.1 cites -- the window's bytes (first byte most
+ * significant, bit 7 high) as a polynomial over GF(2), modulo the irreducible
+ * degree-31 polynomial HG_RABIN_POLY (bit k = coefficient of x^k); the 31-bit
+ * remainder is the window hash. It rolls, so it costs a few operations per
+ * byte instead of one MD5 compression per byte.
+ */
+typedef enum { HG_WIN_MD5 = 0, HG_WIN_RABIN = 1 } hg_window_hash;
+#define HG_RABIN_POLY 0x9E3779BBu
+
+/*
  * Content-defined chunking parameters (Sec. 2.1 "Content-based chunking";
  * min/max chunk sizes as in the Sec. 4.3 set-up). A window of `window` bytes
- * ends at every offset p >= window-1; its hash h is the first four MD5 digest
- * bytes read little-endian; when (h & (2^mask_bits - 1)) == magic the
- * position p + 1 is a candidate cut. Cuts are chosen greedily from offset 0:
- * from chunk start s, the first candidate c with s + min_chunk <= c <=
- * s + max_chunk; with none, s + max_chunk if that is < n, else n.
- * Supported: 1 <= window <= 55, 1 <= mask_bits <= 32, magic < 2^mask_bits,
- * 1 <= min_chunk <= max_chunk.
+ * ends at every offset p >= window-1; its hash h is, for HG_WIN_MD5, the first
+ * four MD5 digest bytes read little-endian, for HG_WIN_RABIN the fingerprint
+ * above; when (h & (2^mask_bits - 1)) == magic the position p + 1 is a
+ * candidate cut. Cuts are chosen greedily from offset 0: from chunk start s,
+ * the first candidate c with s + min_chunk <= c <= s + max_chunk; with none,
+ * s + max_chunk if that is < n, else n.
+ * Supported: 1 <= window <= 55 (MD5) or 64 (Rabin), 1 <= mask_bits <= 32,
+ * magic < 2^mask_bits, 1 <= min_chunk <= max_chunk. The batch and server
+ * calls support HG_WIN_MD5 only (HG_EUNSUPPORTED otherwise).
  */
 typedef struct {
-    uint32_t window;     /* bytes per window (20) */
-    uint32_t mask_bits;  /* low bits of the window hash compared (13) */
-    uint32_t magic;      /* value they must equal (0x0F0F) */
-    uint32_t reserved;   /* must be 0 */
-    uint64_t min_chunk;  /* 2048 */
-    uint64_t max_chunk;  /* 65536 */
+    uint32_t window;      /* bytes per window (20) */
+    uint32_t mask_bits;   /* low bits of the window hash compared (13) */
+    uint32_t magic;       /* value they must equal (0x0F0F) */
+    uint32_t window_hash; /* hg_window_hash (HG_WIN_MD5) */
+    uint64_t min_chunk;   /* 2048 */
+    uint64_t max_chunk;   /* 65536 */
 } hg_cdc_params;
 
 /* Fill p with the defaults used throughout (20, 13, 0x0F0F, 2 KiB, 64 KiB). */

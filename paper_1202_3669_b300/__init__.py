@@ -28,9 +28,13 @@ MD5, SHA1 = HG_MD5, HG_SHA1
 DIGEST_LEN = {MD5: 16, SHA1: 20}
 
 
-def params(window=20, mask_bits=13, magic=0x0F0F, min_chunk=2048, max_chunk=65536) -> hg_cdc_params:
+WIN_MD5, WIN_RABIN = 0, 1
+
+
+def params(window=20, mask_bits=13, magic=0x0F0F, min_chunk=2048, max_chunk=65536,
+           window_hash=WIN_MD5) -> hg_cdc_params:
     p = hg_cdc_params()
-    p.window, p.mask_bits, p.magic, p.reserved = window, mask_bits, magic, 0
+    p.window, p.mask_bits, p.magic, p.window_hash = window, mask_bits, magic, window_hash
     p.min_chunk, p.max_chunk = min_chunk, max_chunk
     return p
 

@@ -28,7 +28,7 @@ class hg_batch_tuning(C.Structure):
 
 class hg_cdc_params(C.Structure):
     _fields_ = [("window", C.c_uint32), ("mask_bits", C.c_uint32), ("magic", C.c_uint32),
-                ("reserved", C.c_uint32), ("min_chunk", C.c_uint64), ("max_chunk", C.c_uint64)]
+                ("window_hash", C.c_uint32), ("min_chunk", C.c_uint64), ("max_chunk", C.c_uint64)]
 
 
 HG_REQ_CDC, HG_REQ_BLOCKS = 0, 1

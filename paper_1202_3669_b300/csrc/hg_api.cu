@@ -12,8 +12,9 @@
 namespace hg {
 
 static int check_params(const hg_cdc_params *p) {
-    if (!p || p->reserved != 0) return HG_EINVAL;
-    if (p->window < 1 || p->window > 55) return HG_EUNSUPPORTED;
+    if (!p || (p->window_hash != HG_WIN_MD5 && p->window_hash != HG_WIN_RABIN)) return HG_EINVAL;
+    if (p->window < 1 || p->window > (p->window_hash == HG_WIN_RABIN ? 64u : 55u))
+        return HG_EUNSUPPORTED;
     if (p->mask_bits < 1 || p->mask_bits > 32) return HG_EINVAL;
     if (p->mask_bits < 32 && (p->magic >> p->mask_bits) != 0) return HG_EINVAL;
     if (p->min_chunk < 1 || p->min_chunk > p->max_chunk) return HG_EINVAL;
@@ -83,7 +84,7 @@ void hg_cdc_default_params(hg_cdc_params *p) {
     p->window = 20;
     p->mask_bits = 13;
     p->magic = 0x0F0F;
-    p->reserved = 0;
+    p->window_hash = HG_WIN_MD5;
     p->min_chunk = 2048;
     p->max_chunk = 65536;
 }
@@ -119,7 +120,8 @@ int hg_init(hg_ctx **out, int device, size_t budget) {
     c->budget = budget ? budget : ((size_t)32 << 30);
     DeviceGuard g(device);
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
-    if (cudaMalloc(&c->d_err, 64) != cudaSuccess || cudaMemset(c->d_err, 0, 64) != cudaSuccess) {
+    if (rabin_prepare() != HG_OK || cudaMalloc(&c->d_err, 64) != cudaSuccess ||
+        cudaMemset(c->d_err, 0, 64) != cudaSuccess) {
         cudaGetLastError();
         if (c->d_err) cudaFree(c->d_err);
         delete c;
@@ -442,7 +444,7 @@ static int run_cdc_hash(hg_ctx *c, int algo, const uint8_t *h_in, const uint8_t 
                               p->min_chunk, p->max_chunk, (uint64_t)algo,
                               (uint64_t)(uintptr_t)d_ends, cap, (uint64_t)(uintptr_t)d_count,
                               (uint64_t)(uintptr_t)d_digests, c->scratch_gen,
-                              (uint64_t)(uintptr_t)h_in, 1, 0};
+                              (uint64_t)(uintptr_t)h_in, 1, p->window_hash};
     if (!c->p_exec || std::memcmp(key, c->p_key, sizeof key)) {
         if (c->p_exec) {
             cudaStreamSynchronize(s);

@@ -390,6 +390,9 @@ int launch_window_range(const uint8_t *d_in, uint64_t n, const hg_cdc_params &p,
                         uint32_t *d_bitmap, uint32_t *d_tile_cnt, uint32_t tile0, uint64_t ntiles,
                         cudaStream_t s, int *d_err) {
     if (ntiles == 0) return HG_OK;
+    if (p.window_hash == HG_WIN_RABIN)
+        return launch_window_rabin_range(d_in, n, p, d_bitmap, d_tile_cnt, tile0, ntiles, s);
+    if (p.window_hash != HG_WIN_MD5) return HG_EINVAL;
     const uint32_t mask = p.mask_bits >= 32 ? 0xffffffffu : ((1u << p.mask_bits) - 1u);
     if (p.window < 1 || p.window > 55) return HG_EUNSUPPORTED;
     switch (p.window) {

@@ -267,6 +267,27 @@ struct Sha1 {
     __device__ __forceinline__ uint32_t out_word(int i) const { return bswap(h[i]); }
 };
 
+// Very few latency-bound digest chains (large fixed blocks: 1024 chains of
+// 1 MiB) run on half warps: a dependent MD5 step measured about 20 cycles
+// with 16 of a warp's lanes active against 27 with all 32 (1 MiB blocks:
+// 98 vs 92 GB/s). With more chains the integer pipes are the limit and full
+// warps win (16384 SHA-1 chains of 64 KiB: 1570 vs 868 GB/s).
+constexpr uint64_t kHalfWarpChainsMax = 4096;
+
+// Task index of this thread when tasks are dealt to the first `lanes` (16 or
+// 32) lanes of every warp; false on the idle lanes.
+__device__ __forceinline__ bool chain_task(uint64_t &i, uint32_t lanes) {
+    const uint32_t lane = threadIdx.x & 31;
+    if (lane >= lanes) return false;
+    i = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32 * lanes + lane;
+    return true;
+}
+
+// Asks for the 16 bytes at p to be brought into L2 (no register result).
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // Digest of the len bytes at msg, which may start at any byte address. Full
 // 64-byte blocks are read as aligned 16-byte vectors; for a message that does
 // not start on a 16-byte boundary they are shifted into place (the aligned
@@ -281,47 +302,40 @@ __device__ void hash_range(const uint8_t *__restrict__ msg, uint64_t len, H &hs)
     const uint32_t sh = (uint32_t)(addr & 15);
     const uint32_t q = sh >> 2, r8 = (sh & 3) * 8;
     const uint4 *p = reinterpret_cast<const uint4 *>(addr - sh);
+    // A chain is one dependent sequence: the loads of block k+1 are issued
+    // before block k is compressed, and an L2 prefetch eight blocks ahead
+    // keeps those loads from waiting on HBM. (Loading two blocks ahead into
+    // registers measured slower for chunk digests: more live registers and
+    // moves per block.)
     if (sh == 0) {
-        // aligned message: four 16-byte loads per block, no shifting. A chain
-        // is one dependent sequence, so the loads run two blocks ahead of the
-        // compression they feed (a block's rounds take less time than a load
-        // from HBM).
+        // aligned message: four 16-byte loads per block, no shifting
         uint4 a0 = make_uint4(0, 0, 0, 0), a1 = a0, a2 = a0, a3 = a0;
-        uint4 b0 = a0, b1 = a0, b2 = a0, b3 = a0;
-        if (nfull > 0) { a0 = __ldg(p); a1 = __ldg(p + 1); a2 = __ldg(p + 2); a3 = __ldg(p + 3); }
-        if (nfull > 1) { b0 = __ldg(p + 4); b1 = __ldg(p + 5); b2 = __ldg(p + 6); b3 = __ldg(p + 7); }
+        if (nfull) { a0 = __ldg(p); a1 = __ldg(p + 1); a2 = __ldg(p + 2); a3 = __ldg(p + 3); }
         for (uint64_t k = 0; k < nfull; k++) {
-            uint4 c0 = b0, c1 = b1, c2 = b2, c3 = b3;
-            if (k + 2 < nfull) {
-                const uint4 *q4 = p + 4 * (k + 2);
-                c0 = __ldg(q4); c1 = __ldg(q4 + 1); c2 = __ldg(q4 + 2); c3 = __ldg(q4 + 3);
-            }
             const uint32_t M[16] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w,
                                     a2.x, a2.y, a2.z, a2.w, a3.x, a3.y, a3.z, a3.w};
+            if (k + 8 < nfull) prefetch_l2(p + 4 * (k + 8));
+            if (k + 1 < nfull) {
+                const uint4 *q4 = p + 4 * (k + 1);
+                a0 = __ldg(q4); a1 = __ldg(q4 + 1); a2 = __ldg(q4 + 2); a3 = __ldg(q4 + 3);
+            }
             hs.compress(M);
-            a0 = b0; a1 = b1; a2 = b2; a3 = b3;
-            b0 = c0; b1 = c1; b2 = c2; b3 = c3;
         }
     } else {
-        // unaligned message: five aligned loads per block, shifted into place;
-        // the loads run two blocks ahead as above
+        // unaligned message: five aligned loads per block, shifted into place
         uint4 x0 = make_uint4(0, 0, 0, 0), x1 = x0, x2 = x0, x3 = x0, x4 = x0;
-        uint4 y0 = x0, y1 = x0, y2 = x0, y3 = x0, y4 = x0;
-        if (nfull > 0) {
+        if (nfull) {
             x0 = __ldg(p); x1 = __ldg(p + 1); x2 = __ldg(p + 2); x3 = __ldg(p + 3); x4 = __ldg(p + 4);
-        }
-        if (nfull > 1) {
-            y0 = __ldg(p + 4); y1 = __ldg(p + 5); y2 = __ldg(p + 6); y3 = __ldg(p + 7); y4 = __ldg(p + 8);
         }
         for (uint64_t k = 0; k < nfull; k++) {
             const uint32_t v[20] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w,
                                     x2.x, x2.y, x2.z, x2.w, x3.x, x3.y, x3.z, x3.w,
                                     x4.x, x4.y, x4.z, x4.w};
-            x0 = y0; x1 = y1; x2 = y2; x3 = y3; x4 = y4;
-            if (k + 2 < nfull) {
-                const uint4 *q4 = p + 4 * (k + 2);
-                y0 = __ldg(q4); y1 = __ldg(q4 + 1); y2 = __ldg(q4 + 2); y3 = __ldg(q4 + 3);
-                y4 = __ldg(q4 + 4);
+            if (k + 8 < nfull) prefetch_l2(p + 4 * (k + 8));
+            if (k + 1 < nfull) {
+                const uint4 *q4 = p + 4 * (k + 1);
+                x0 = __ldg(q4); x1 = __ldg(q4 + 1); x2 = __ldg(q4 + 2); x3 = __ldg(q4 + 3);
+                x4 = __ldg(q4 + 4);
             }
             // shift by q words, then by r8 bits
             uint32_t u[17];

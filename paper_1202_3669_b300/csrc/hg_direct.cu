@@ -58,15 +58,16 @@ __global__ void __launch_bounds__(128, 16) k_hash_blocks_aligned(const uint8_t *
 }
 
 // Few blocks (fewer chains than it takes to fill the integer pipes): each
-// block is a latency-bound chain, so the chain form of the step, loads two
-// blocks ahead (hash_range) and no register cap; small CTAs spread the chains
-// over the SMs.
+// block is a latency-bound chain, so the chain form of the step, loads ahead
+// (hash_range), no register cap, small CTAs spread over the SMs, and half
+// warps when the chains are very few (chain_task).
 template <class H>
 __global__ void __launch_bounds__(64) k_hash_blocks_aligned_few(const uint8_t *__restrict__ in,
                                                                 uint64_t block, uint64_t nfull,
+                                                                uint32_t lanes,
                                                                 uint8_t *__restrict__ out) {
-    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nfull) return;
+    uint64_t i;
+    if (!chain_task(i, lanes) || i >= nfull) return;
     H hs;
     hash_range(in + i * block, block, hs);
     store_digest(hs, out + i * H::kDigest);
@@ -174,11 +175,14 @@ int launch_hash_blocks(int algo, const uint8_t *d_in, uint64_t n, uint64_t block
             if (algo == HG_MD5) k_hash_blocks_aligned<Md5><<<grid, 128, 0, s>>>(d_in, block, nfull, d_digests);
             else k_hash_blocks_aligned<Sha1><<<grid, 128, 0, s>>>(d_in, block, nfull, d_digests);
         } else if (nfull) {
-            const unsigned grid = (unsigned)((nfull + 63) / 64);
+            const uint32_t lanes = nfull <= kHalfWarpChainsMax ? 16 : 32;
+            const unsigned grid = chain_grid(nfull, lanes, 64);
             if (algo == HG_MD5)
-                k_hash_blocks_aligned_few<Md5Chain><<<grid, 64, 0, s>>>(d_in, block, nfull, d_digests);
+                k_hash_blocks_aligned_few<Md5Chain><<<grid, 64, 0, s>>>(d_in, block, nfull, lanes,
+                                                                      d_digests);
             else
-                k_hash_blocks_aligned_few<Sha1><<<grid, 64, 0, s>>>(d_in, block, nfull, d_digests);
+                k_hash_blocks_aligned_few<Sha1><<<grid, 64, 0, s>>>(d_in, block, nfull, lanes,
+                                                                  d_digests);
         }
         if (nfull < nblk) {
             const uint64_t lo = nfull * block;

@@ -41,6 +41,12 @@ constexpr int kWinThreads = 256;
 constexpr int kWinPerThread = 32;
 constexpr uint64_t kWinTile = (uint64_t)kWinThreads * kWinPerThread;
 
+// Grid of a chain kernel whose tasks are dealt to `lanes` lanes of each warp
+// (see chain_task) for ntask tasks and `threads` threads per CTA.
+inline unsigned chain_grid(uint64_t ntask, unsigned lanes, unsigned threads) {
+    return (unsigned)((ntask * (32 / lanes) + threads - 1) / threads);
+}
+
 // Candidate-list capacity used by hg_cdc_boundaries for an n-byte input. The
 // expected density is 2^-mask_bits per byte; denser inputs fall back to
 // scanning the bitmap during selection.
@@ -97,6 +103,13 @@ int launch_compact(const uint32_t *d_bitmap, uint64_t n, const uint32_t *d_tile_
 int launch_window_range(const uint8_t *d_in, uint64_t n, const hg_cdc_params &p,
                         uint32_t *d_bitmap, uint32_t *d_tile_cnt, uint32_t tile0, uint64_t ntiles,
                         cudaStream_t s, int *d_err);
+// Rabin fingerprint window (hg_rabin.cu): same bitmap and tile counts.
+// rabin_prepare: per-device kernel set-up for the current device, to be
+// called outside stream capture (hg_init does).
+int rabin_prepare();
+int launch_window_rabin_range(const uint8_t *d_in, uint64_t n, const hg_cdc_params &p,
+                              uint32_t *d_bitmap, uint32_t *d_tile_cnt, uint32_t tile0,
+                              uint64_t ntiles, cudaStream_t s);
 // n: bytes in d_in; n_sel: end of the stream for selection (n, or ~0 when the
 // stream continues beyond d_in).
 int launch_pipe_segment(const uint8_t *d_in, uint64_t n, uint64_t n_sel, const hg_cdc_params &p,

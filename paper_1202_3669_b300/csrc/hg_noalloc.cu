@@ -72,8 +72,10 @@ using namespace hg;
 extern "C" int hg_cdc_boundaries_static(const uint8_t *d_in, uint64_t n, const hg_cdc_params *p,
                                         uint64_t *d_ends, uint64_t cap, uint64_t *d_count,
                                         void *stream) {
-    if (!p || p->reserved != 0 || !d_count || (cap && !d_ends)) return HG_EINVAL;
-    if (p->window < 1 || p->window > 55) return HG_EUNSUPPORTED;
+    if (!p || (p->window_hash != HG_WIN_MD5 && p->window_hash != HG_WIN_RABIN) || !d_count ||
+        (cap && !d_ends))
+        return HG_EINVAL;
+    if (p->window < 1 || p->window > (p->window_hash == HG_WIN_RABIN ? 64u : 55u)) return HG_EUNSUPPORTED;
     if (p->mask_bits < 1 || p->mask_bits > 32) return HG_EINVAL;
     if (p->mask_bits < 32 && (p->magic >> p->mask_bits) != 0) return HG_EINVAL;
     if (p->min_chunk < 1 || p->min_chunk > p->max_chunk) return HG_EINVAL;

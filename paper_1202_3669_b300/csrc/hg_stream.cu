@@ -90,7 +90,8 @@ int hg_stream_open(hg_ctx *ctx, int algo, const hg_cdc_params *p, uint64_t max_f
     if (!ctx || !p || !out || (algo != HG_MD5 && algo != HG_SHA1) || max_feed_bytes == 0)
         return HG_EINVAL;
     *out = nullptr;
-    if (p->reserved || p->window < 1 || p->window > 55 || p->mask_bits < 1 || p->mask_bits > 32 ||
+    if ((p->window_hash != HG_WIN_MD5 && p->window_hash != HG_WIN_RABIN) || p->window < 1 ||
+        p->window > (p->window_hash == HG_WIN_RABIN ? 64u : 55u) || p->mask_bits < 1 || p->mask_bits > 32 ||
         (p->mask_bits < 32 && (p->magic >> p->mask_bits)) || p->min_chunk < 1 ||
         p->min_chunk > p->max_chunk)
         return HG_EINVAL;

@@ -1,0 +1,156 @@
+"""GPU parity of the Rabin fingerprint window (HG_WIN_RABIN) against the CPU oracle.
+
+The window bitmap, candidates, boundaries and chunk digests are integer
+results: every comparison is exact. The interior fast path (aligned input,
+specialised window lengths) and the byte-load path (edges, unaligned input,
+other window lengths) are both covered.
+"""
+import hashlib
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from gen import inputs as G
+from tests.gpu_util import bitmap_to_cuts, to_device
+from tests.pins import check_chunking
+
+pytestmark = pytest.mark.gpu
+R = oracle.WIN_RABIN
+
+
+@pytest.fixture(scope="module")
+def hg():
+    import paper_1202_3669_b300 as hgb
+    ctx = hgb.Context(0)
+    yield ctx
+    ctx.close()
+
+
+def P(**kw):
+    import paper_1202_3669_b300 as hgb
+    kw.setdefault("window", 48)
+    return hgb.params(window_hash=hgb.WIN_RABIN, **kw)
+
+
+SIZES = [0, 1, 47, 48, 49, 100, 8191, 8192, 32768, 32769, 8192 * 7 + 77, 300_001, (1 << 20) + 13]
+WINDOWS = [(48, 6, 0x2A), (16, 5, 0x11), (20, 4, 0x3), (24, 5, 0x1F), (32, 6, 0x20), (64, 5, 0),
+           (1, 3, 0x5), (7, 4, 0xA), (33, 6, 0x21), (55, 5, 0x1), (48, 13, 0x0F0F)]
+
+
+@pytest.mark.parametrize("n", SIZES)
+@pytest.mark.parametrize("window,mask_bits,magic", WINDOWS)
+def test_window_bitmap(hg, n, window, mask_bits, magic):
+    data = G.uniform_bytes(n, seed=n * 5 + window)
+    want = oracle.window_candidates(data, window, mask_bits, magic, nthreads=8, kind=R)
+    for off in (0, 3):
+        bm = hg.window_bitmap(to_device(data, off), P(window=window, mask_bits=mask_bits, magic=magic))
+        got = bitmap_to_cuts(bm, n)
+        assert np.array_equal(got, want), (off, got[:10], want[:10])
+    hg.sync()
+
+
+@pytest.mark.parametrize("n", [0, 5000, 3 << 20, (20 << 20) + 12345])
+@pytest.mark.parametrize("algo", [oracle.MD5, oracle.SHA1])
+def test_cdc_hash(hg, n, algo):
+    data = G.uniform_bytes(n, seed=n + 17)
+    ends, cnt, dg = hg.cdc_hash(to_device(data, 0 if n % 2 else 5), algo, P(mask_bits=13, magic=0x0F0F))
+    hg.sync()
+    k = int(cnt.item())
+    cands = oracle.window_candidates(data, 48, 13, 0x0F0F, nthreads=16, kind=R)
+    want = oracle.select(cands, data.size, 2048, 65536)
+    assert np.array_equal(ends[:k].cpu().numpy().astype(np.uint64), want)
+    check_chunking(want.tolist(), cands.tolist(), n, 2048, 65536)
+    assert np.array_equal(dg[:k].cpu().numpy(), oracle.hash_chunks(algo, data, want))
+
+
+def test_cdc_segmented_text_like(hg):
+    """Above 64 MiB hg_cdc_hash runs segments with a carried open chunk."""
+    data = G.text_like_bytes((70 << 20) + 333, seed=5)
+    p = P(window=32, mask_bits=11, magic=0x155, min_chunk=512, max_chunk=16384)
+    ends, cnt, dg = hg.cdc_hash(to_device(data), oracle.MD5, p)
+    hg.sync()
+    k = int(cnt.item())
+    want = oracle.cdc(data, 32, 11, 0x155, 512, 16384, nthreads=16, kind=R)
+    assert np.array_equal(ends[:k].cpu().numpy().astype(np.uint64), want)
+    assert np.array_equal(dg[:k].cpu().numpy(), oracle.hash_chunks(oracle.MD5, data, want))
+
+
+def test_boundaries_dense_and_static(hg):
+    data = G.uniform_bytes((3 << 20) + 7, seed=19)
+    p = P(window=24, mask_bits=2, magic=1, min_chunk=64, max_chunk=4096)    # list overflows
+    want = oracle.cdc(data, 24, 2, 1, 64, 4096, nthreads=16, kind=R)
+    ends, cnt = hg.cdc_boundaries(to_device(data), p)
+    hg.sync()
+    assert np.array_equal(ends[:int(cnt.item())].cpu().numpy().astype(np.uint64), want)
+    import ctypes as C
+    from paper_1202_3669_b300 import _lib
+    d1 = to_device(data, 1)
+    cap = data.size // 64 + 2
+    e_st = torch.empty(cap, dtype=torch.int64, device="cuda")
+    c_st = torch.zeros(1, dtype=torch.int64, device="cuda")
+    rc = _lib.lib.hg_cdc_boundaries_static(d1.data_ptr(), data.size, C.byref(p), e_st.data_ptr(),
+                                           cap, c_st.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    assert rc == 0
+    torch.cuda.synchronize()
+    assert np.array_equal(e_st[:int(c_st.item())].cpu().numpy().astype(np.uint64), want)
+
+
+def test_stream_equals_one_shot(hg):
+    import paper_1202_3669_b300 as hgb
+    data = G.uniform_bytes((9 << 20) + 5, seed=23)
+    p = P()
+    want = oracle.cdc(data, 48, 13, 0x0F0F, nthreads=16, kind=R)
+    st = hgb.CdcStream(hg, hgb.SHA1, p, max_feed=4 << 20)
+    d = to_device(data)
+    rng = np.random.default_rng(5)
+    pos, ends, digs = 0, [], []
+    while pos < data.size:
+        k = int(min(data.size - pos, rng.integers(1, 4 << 20)))
+        e, g = st.feed(d[pos:pos + k])
+        ends.append(e); digs.append(g)
+        pos += k
+    e, g = st.close()
+    ends.append(e); digs.append(g)
+    got = np.concatenate([x.cpu().numpy().astype(np.uint64) for x in ends])
+    assert np.array_equal(got, want)
+    dg = np.concatenate([x.cpu().numpy() for x in digs])
+    assert np.array_equal(dg, oracle.hash_chunks(oracle.SHA1, data, want))
+
+
+def test_config_rabin_1gib(hg):
+    """1 GiB uniform (seed 4), default Rabin parameters (48-byte window): candidates
+    equal the oracle's on sampled 1 MiB ranges, ends equal the oracle's selection
+    over the whole candidate list, sampled digests equal hashlib's."""
+    n = 1 << 30
+    data = G.uniform_bytes(n, seed=4)
+    d = to_device(data)
+    p = P()
+    cands, ccnt = hg.cdc_candidates(d, p, cap=n // 1024)
+    hg.sync()
+    cands = cands[:int(ccnt.item())].cpu().numpy().astype(np.uint64)
+    rng = np.random.default_rng(12)
+    for a in [0, n - (1 << 20)] + sorted(rng.integers(0, n - (1 << 20), 10).tolist()):
+        lo = max(0, a - 47)
+        hi = a + (1 << 20)
+        sub = oracle.window_candidates(data[lo:hi], 48, 13, 0x0F0F, nthreads=16, kind=R) + np.uint64(lo)
+        sub = sub[sub > a]
+        assert np.array_equal(cands[(cands > a) & (cands <= hi)], sub), a
+    want = oracle.select(cands, n, 2048, 65536)
+    ends, cnt, dg = hg.cdc_hash(d, oracle.MD5, p)
+    hg.sync()
+    k = int(cnt.item())
+    assert np.array_equal(ends[:k].cpu().numpy().astype(np.uint64), want)
+    dgn = dg[:k].cpu().numpy()
+    for i in sorted(rng.integers(0, k, 200).tolist()) + [0, k - 1]:
+        s = int(want[i - 1]) if i else 0
+        assert dgn[i].tobytes() == hashlib.md5(data[s:int(want[i])].tobytes()).digest(), i
+
+
+def test_batch_and_server_refuse_rabin(hg):
+    import paper_1202_3669_b300 as hgb
+    with pytest.raises(hgb.HashGPUError):
+        hgb.Batch(hg, np.array([0, 1000, 5000], np.uint64), P())
+    with pytest.raises(hgb.HashGPUError):
+        hgb.Server(hg, device_budget=256 << 20, max_wave_bytes=16 << 20, p=P())
