@@ -175,6 +175,24 @@ def cdc(data, window: int = 20, mask_bits: int = 13, magic: int = 0x0F0F,
     return select(c, a.size, min_chunk, max_chunk, L)
 
 
+def blockmap_hits(known_digests, query_digests) -> np.ndarray:
+    """Similarity detection by block identifiers (Sec. 2.1: comparing hash values
+    detects identical blocks; Sec. 4.3: the share of a new version's data found in
+    chunks already stored): hit[i] is True when query digest i equals one of the
+    known digests. Plain set membership over the full digest bytes."""
+    seen = {bytes(d) for d in np.asarray(known_digests, dtype=np.uint8)}
+    return np.array([bytes(d) in seen for d in np.asarray(query_digests, dtype=np.uint8)], dtype=bool)
+
+
+def shared_bytes(known_digests, ends, query_digests) -> tuple[int, int]:
+    """(number of query chunks found, bytes in them); chunk i of the queried version
+    is [ends[i-1] (0 for i = 0), ends[i])."""
+    hits = blockmap_hits(known_digests, query_digests)
+    e = np.asarray(ends, dtype=np.int64)
+    sizes = np.diff(np.concatenate([[0], e])) if e.size else np.zeros(0, np.int64)
+    return int(hits.sum()), int(sizes[hits].sum()) if hits.size else 0
+
+
 def shared_fraction(ends_v1, dig_v1, ends_v2, dig_v2) -> float:
     """Bytes of v2 in chunks whose digest also names a v1 chunk, over len(v2)."""
     seen = {bytes(d) for d in np.asarray(dig_v1)}
