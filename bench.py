@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the direct/batch/serve/CPU legs")
-    ap.add_argument("--leg", default=None, choices=["direct", "batch", "serve", "rabin"],
+    ap.add_argument("--leg", default=None, choices=["direct", "batch", "serve", "rabin", "blockmap"],
                     help="run only this extra leg (for profiling) and print its result")
     ap.add_argument("--batch-files", type=int, default=4096,
                     help="batch leg: use only the first N files of the 4096-file workload")
@@ -261,6 +261,8 @@ def main():
             res = batch_leg(hgb, ctx, dev, flush, nfiles=args.batch_files)
         elif args.leg == "rabin":
             res = rabin_leg(hgb, dev, flush)
+        elif args.leg == "blockmap":
+            res = blockmap_leg(hgb, ctx, dev, flush)
         else:
             res = serve_leg(hgb, ctx, batch_leg(hgb, ctx, dev, flush)["batched_graph_GBps"])
         print(json.dumps({"leg": args.leg, "result": res}), flush=True)
@@ -446,6 +448,7 @@ def main():
     if not args.no_extras and rank == 0:
         extras["direct"] = direct_leg(hgb, ctxs[0], dev, flush)
         extras["rabin"] = rabin_leg(hgb, dev, flush)
+        extras["blockmap"] = blockmap_leg(hgb, ctxs[0], dev, flush)
         extras["batch"] = batch_leg(hgb, ctxs[0], dev, flush)
         extras["serve"] = serve_leg(hgb, ctxs[0], extras["batch"]["batched_graph_GBps"])
         extras["cpu_baseline"] = cpu_baseline(versions)
@@ -475,7 +478,7 @@ def main():
                "step_ms_p50": statistics.median(step_ms), "step_ms_max": max(step_ms),
                "unpipelined": {"GBps": nbytes / (t_two / 1e3) / 1e9, "ms_per_step": t_two,
                                "calls": "hg_cdc_boundaries + hg_hash_chunks"}}
-        for k in ("direct", "rabin", "batch", "serve"):
+        for k in ("direct", "rabin", "blockmap", "batch", "serve"):
             if k in extras:
                 out[k] = extras[k]
         print(json.dumps(out), flush=True)
@@ -581,6 +584,44 @@ def rabin_leg(hgb, dev, flush, steps=50):
             "chunks": [k0, k1], "shared_fraction": shared / versions[1].size,
             "params": {"window": 48, "mask_bits": 13, "magic": 0x0F0F, "min": 2048, "max": 65536,
                        "window_hash": "rabin (degree-31 polynomial 0x9E3779BB)", "digest": "md5"}}
+
+
+def blockmap_leg(hgb, ctx, dev, flush, n=1 << 24):
+    """Device block map: insert n random MD5-sized digests, then look up n digests of which
+    half are stored (chunk sizes given, so found bytes are summed too). Kernel time with CUDA
+    events; digests per second."""
+    import torch
+    g = np.random.default_rng(13)
+    known = torch.from_numpy(g.integers(0, 256, (n, 16), dtype=np.uint8)).to(dev)
+    pick = torch.from_numpy(g.integers(0, n, n // 2)).to(dev)
+    fresh = torch.from_numpy(g.integers(0, 256, (n - n // 2, 16), dtype=np.uint8)).to(dev)
+    queries = torch.cat([known[pick], fresh])
+    ends = torch.cumsum(torch.from_numpy(g.integers(1, 65536, n)).to(dev), 0)
+    s = torch.cuda.current_stream(dev)
+    ins, look = [], []
+    m = hgb.BlockMap(ctx, hgb.MD5, capacity=n)
+    for i in range(4):
+        m.clear(stream=s)
+        flush.zero_()
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a.record(s)
+        m.insert(known, stream=s)
+        b.record(s)
+        hits, res = m.lookup(queries, ends=ends, want_hits=True, stream=s)
+        c.record(s)
+        if i:
+            ins.append((a, b))
+            look.append((b, c))
+    torch.cuda.synchronize()
+    ctx.sync()
+    found = int(res[0].item())
+    m.close()
+    t_ins = sum(x.elapsed_time(y) for x, y in ins) / len(ins) / 1e3
+    t_look = sum(x.elapsed_time(y) for x, y in look) / len(look) / 1e3
+    return {"digests": n, "insert_Mdigests_per_s": n / t_ins / 1e6, "insert_ms": t_ins * 1e3,
+            "lookup_Mdigests_per_s": n / t_look / 1e6, "lookup_ms": t_look * 1e3,
+            "found": found, "slots": 2 * n,
+            "note": "random 16-byte digests; table 2n slots x 24 B; lookups half hits"}
 
 
 def batch_leg(hgb, ctx, dev, flush, nfiles=4096):

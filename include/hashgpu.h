@@ -384,6 +384,41 @@ int hg_server_replay(hg_server *srv, const hg_request *reqs, const uint64_t *arr
                      uint32_t nreq, uint64_t *latency_ns, uint64_t *span_ns);
 
 /*
+ * Device block map: similarity detection by digests (Sec. 2.1: identical
+ * blocks have equal identifiers; Sec. 4.3: the share of a new version found in
+ * chunks already stored). A hash table of distinct digests (algo fixes the
+ * digest length, 16 or 20 bytes) in device memory, built and probed by
+ * kernels, so a version's chunk digests are compared with everything stored
+ * before without leaving the device. Digest arrays are rows of dlen bytes,
+ * 4-byte aligned, as written by hg_hash_chunks / hg_cdc_hash.
+ *
+ * hg_blockmap_create: room for `capacity` distinct digests (2*capacity slots
+ *   or more, 24 bytes each, counted against the context budget: HG_ENOMEM).
+ * hg_blockmap_insert: adds count digests (min(count, *d_count) when d_count
+ *   is not NULL); a digest already stored is not added again. Inserting more
+ *   distinct digests than there are slots records HG_ECAPACITY in the context
+ *   error word (read by hg_sync). Inserts and lookups on different streams
+ *   must be ordered by the caller.
+ * hg_blockmap_lookup: for query digest i, d_hits[i] = 1 if it is stored,
+ *   else 0 (d_hits may be NULL); d_result[0] = number found and, when d_ends
+ *   (the queried version's chunk ends) is not NULL, d_result[1] = bytes in the
+ *   chunks found (d_result, 8-byte aligned, may be NULL; not both NULL).
+ * hg_blockmap_count: enqueues a copy of the number of distinct digests stored
+ *   to *d_out (device uint64).
+ * hg_blockmap_clear: empties the map (stream-ordered).
+ */
+typedef struct hg_blockmap hg_blockmap;
+int hg_blockmap_create(hg_ctx *ctx, int algo, uint64_t capacity, hg_blockmap **out);
+int hg_blockmap_insert(hg_blockmap *map, const uint8_t *d_digests, uint64_t count,
+                       const uint64_t *d_count, void *stream);
+int hg_blockmap_lookup(hg_blockmap *map, const uint8_t *d_digests, const uint64_t *d_ends,
+                       uint64_t count, const uint64_t *d_count, uint8_t *d_hits,
+                       uint64_t *d_result, void *stream);
+int hg_blockmap_count(hg_blockmap *map, uint64_t *d_out, void *stream);
+int hg_blockmap_clear(hg_blockmap *map, void *stream);
+int hg_blockmap_destroy(hg_blockmap *map);
+
+/*
  * Chunk boundaries without allocating: the same result as hg_cdc_boundaries,
  * for callers that cannot call cudaMalloc -- a write path that must not stall
  * on the device-wide synchronisation cudaMalloc/cudaFree can cause, a process

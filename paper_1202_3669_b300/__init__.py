@@ -22,7 +22,9 @@ from ._lib import (HG_MD5, HG_SHA1, HashGPUError, check, default_params,  # noqa
                    hg_server_config, hg_server_create, hg_server_default_config, hg_server_destroy,
                    hg_server_get_stats, hg_server_replay, hg_server_stats, hg_server_wait_any,
                    hg_submit, hg_cdc_hash, hg_cdc_hash_plan, hg_cdc_hash_h2d, hg_stream_open,
-                   hg_stream_feed, hg_stream_close, hg_stream_destroy)
+                   hg_stream_feed, hg_stream_close, hg_stream_destroy, hg_blockmap_create,
+                   hg_blockmap_insert, hg_blockmap_lookup, hg_blockmap_count, hg_blockmap_clear,
+                   hg_blockmap_destroy)
 
 MD5, SHA1 = HG_MD5, HG_SHA1
 DIGEST_LEN = {MD5: 16, SHA1: 20}
@@ -413,5 +415,49 @@ class CdcStream:
         try:
             if self.h:
                 hg_stream_destroy(self.h)
+        except Exception:
+            pass
+
+
+class BlockMap:
+    """Device hash table of distinct digests (hg_blockmap_*): similarity detection."""
+
+    def __init__(self, ctx: Context, algo: int = MD5, capacity: int = 1 << 20):
+        self.ctx, self.algo = ctx, algo
+        self.h = hg_blockmap_create(ctx.h, algo, capacity)
+
+    def insert(self, digests: torch.Tensor, count: torch.Tensor | None = None, stream=None):
+        check(hg_blockmap_insert(self.h, _ptr(digests), digests.shape[0] if digests.dim() else 0,
+                                 _ptr(count) if count is not None else None, _stream(stream)),
+              "hg_blockmap_insert")
+
+    def lookup(self, digests: torch.Tensor, ends: torch.Tensor | None = None,
+               count: torch.Tensor | None = None, want_hits: bool = True, stream=None):
+        """(hits uint8[n] or None, result int64[2] = {found, bytes found})."""
+        n = digests.shape[0]
+        hits = torch.empty(max(n, 1), dtype=torch.uint8, device=self.ctx.device) if want_hits else None
+        res = torch.empty(2, dtype=torch.int64, device=self.ctx.device)
+        check(hg_blockmap_lookup(self.h, _ptr(digests), _ptr(ends) if ends is not None else None, n,
+                                 _ptr(count) if count is not None else None,
+                                 _ptr(hits) if hits is not None else None, _ptr(res), _stream(stream)),
+              "hg_blockmap_lookup")
+        return (hits[:n] if hits is not None else None), res
+
+    def count(self, stream=None) -> torch.Tensor:
+        out = torch.empty(1, dtype=torch.int64, device=self.ctx.device)
+        check(hg_blockmap_count(self.h, _ptr(out), _stream(stream)), "hg_blockmap_count")
+        return out
+
+    def clear(self, stream=None):
+        check(hg_blockmap_clear(self.h, _stream(stream)), "hg_blockmap_clear")
+
+    def close(self):
+        if self.h:
+            hg_blockmap_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
         except Exception:
             pass

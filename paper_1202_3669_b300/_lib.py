@@ -69,6 +69,12 @@ SIGNATURES = {
     "hg_scratch_bytes": (_u64, [_vp]),
     "hg_hash_blocks": (_i32, [_vp, _i32, _vp, _u64, _u64, _vp, _vp, _vp]),
     "hg_hash_blocks_pmd": (_i32, [_vp, _i32, _vp, _u64, _u64, _u64, _vp, _vp, _vp]),
+    "hg_blockmap_create": (_i32, [_vp, _i32, _u64, _vp]),
+    "hg_blockmap_insert": (_i32, [_vp, _vp, _u64, _vp, _vp]),
+    "hg_blockmap_lookup": (_i32, [_vp, _vp, _vp, _u64, _vp, _vp, _vp, _vp]),
+    "hg_blockmap_count": (_i32, [_vp, _vp, _vp]),
+    "hg_blockmap_clear": (_i32, [_vp, _vp]),
+    "hg_blockmap_destroy": (_i32, [_vp]),
     "hg_window_bitmap": (_i32, [_vp, _vp, _u64, C.POINTER(hg_cdc_params), _vp, _vp]),
     "hg_cdc_candidates": (_i32, [_vp, _vp, _u64, C.POINTER(hg_cdc_params), _vp, _u64, _vp, _vp]),
     "hg_cdc_boundaries": (_i32, [_vp, _vp, _u64, C.POINTER(hg_cdc_params), _vp, _u64, _vp, _vp]),
@@ -293,6 +299,32 @@ def hg_cdc_hash_plan(n, bounds_ptr, max_n) -> int:
 def hg_cdc_hash_h2d(ctx, algo, h_in, d_in, n, params, d_ends, cap, d_count, d_digests, stream) -> int:
     return lib.hg_cdc_hash_h2d(ctx, algo, h_in, d_in, n, C.byref(params), d_ends, cap, d_count,
                                d_digests, stream)
+
+
+def hg_blockmap_create(ctx, algo, capacity) -> int:
+    h = _vp()
+    check(lib.hg_blockmap_create(ctx, algo, capacity, C.byref(h)), "hg_blockmap_create")
+    return h.value
+
+
+def hg_blockmap_insert(m, d_digests, count, d_count, stream) -> int:
+    return lib.hg_blockmap_insert(m, d_digests, count, d_count, stream)
+
+
+def hg_blockmap_lookup(m, d_digests, d_ends, count, d_count, d_hits, d_result, stream) -> int:
+    return lib.hg_blockmap_lookup(m, d_digests, d_ends, count, d_count, d_hits, d_result, stream)
+
+
+def hg_blockmap_count(m, d_out, stream) -> int:
+    return lib.hg_blockmap_count(m, d_out, stream)
+
+
+def hg_blockmap_clear(m, stream) -> int:
+    return lib.hg_blockmap_clear(m, stream)
+
+
+def hg_blockmap_destroy(m) -> int:
+    return lib.hg_blockmap_destroy(m)
 
 
 def hg_stream_open(ctx, algo, params, max_feed) -> int:
