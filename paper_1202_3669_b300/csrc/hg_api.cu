@@ -302,7 +302,7 @@ static int pipe_setup(hg_ctx *c) {
               cudaStreamCreateWithPriority(&c->p_sel, cudaStreamNonBlocking, greatest) == cudaSuccess &&
               cudaEventCreateWithFlags(&c->p_fork, cudaEventDisableTiming) == cudaSuccess &&
               cudaEventCreateWithFlags(&c->p_done_sel, cudaEventDisableTiming) == cudaSuccess &&
-              cudaMalloc(&c->d_pipe, sizeof(PipeState)) == cudaSuccess;
+              cudaMalloc(&c->d_pipe, sizeof(PipeState) + kLongListBytes) == cudaSuccess;
     for (int i = 0; ok && i < kMaxSeg; i++)   // one digest stream per segment: they never wait on each other
         ok = cudaStreamCreateWithPriority(&c->p_hash[i], cudaStreamNonBlocking, greatest) == cudaSuccess &&
              cudaEventCreateWithFlags(&c->p_join[i], cudaEventDisableTiming) == cudaSuccess;
@@ -314,7 +314,7 @@ static int pipe_setup(hg_ctx *c) {
         cudaGetLastError();
         return HG_ECUDA;
     }
-    c->held += sizeof(PipeState);
+    c->held += sizeof(PipeState) + kLongListBytes;
     c->pipe_ready = true;
     return HG_OK;
 }
@@ -367,7 +367,9 @@ static int enqueue_cdc_hash(hg_ctx *c, int algo, const uint8_t *d_in, uint64_t n
     const int nseg = (int)b.size() - 1;
     if (nseg > kMaxSeg) return HG_EUNSUPPORTED;
     PipeBufs pb{c->d_bitmap, c->d_tile_cnt, c->d_tile_off, c->d_cands, c->cand_cap,
-                d_ends, cap, d_digests, (PipeState *)c->d_pipe, c->d_err};
+                d_ends, cap, d_digests, (PipeState *)c->d_pipe, c->d_err,
+                reinterpret_cast<uint32_t *>(static_cast<char *>(c->d_pipe) + sizeof(PipeState)),
+                long_chains(c->num_sms)};
     int r;
     cudaEventRecord(c->p_fork, s);
     cudaStreamWaitEvent(c->p_win, c->p_fork, 0);

@@ -257,9 +257,10 @@ __device__ void select_serial(const uint64_t *__restrict__ cands, uint64_t ncand
 __global__ void __launch_bounds__(kSelThreads) k_select_seg(
     const uint64_t *__restrict__ cands, uint64_t cand_cap, const uint32_t *__restrict__ bitmap,
     uint64_t n, uint64_t L, uint64_t mn, uint64_t mx, uint64_t *__restrict__ ends, uint64_t cap,
-    PipeState *st, int seg) {
-    __shared__ uint64_t s_carry, s_count, s_ncand, s_new;
-    __shared__ uint32_t s_k0;
+    PipeState *st, int seg, uint32_t *__restrict__ long_idx, uint32_t klong) {
+    __shared__ uint64_t s_carry, s_count, s_ncand, s_new, s_thr;
+    __shared__ uint32_t s_k0, s_nlong;
+    __shared__ uint32_t hist[128];
     const int t = threadIdx.x;
     if (t == 0) {
         s_carry = st->carry;
@@ -275,7 +276,9 @@ __global__ void __launch_bounds__(kSelThreads) k_select_seg(
         }
         s_k0 = k0;
         s_new = 0;
+        s_nlong = 0;
     }
+    if (t < 128) hist[t] = 0;
     __syncthreads();
     const uint64_t count = s_count, carry = s_carry;
     const uint64_t room = cap > count ? cap - count : 0;
@@ -284,33 +287,77 @@ __global__ void __launch_bounds__(kSelThreads) k_select_seg(
             uint64_t idx = 0;
             const uint64_t last = select_thread_bitmap(bitmap, carry, n, mn, mx,
                                                        WriteEmit{ends + count, room, &idx, 0}, L);
-            st->count = count + idx;
+            s_new = idx;
             st->carry = last;
-            st->seg_cnt[seg + 1] = count + idx;
         }
-        return;
+    } else {
+        select_block(cands + s_k0, (uint32_t)(s_ncand - s_k0), carry, n, mn, mx, ends + count, room,
+                     &s_new, L, 0);
     }
-    const uint32_t k0 = s_k0;
-    select_block(cands + k0, (uint32_t)(s_ncand - k0), carry, n, mn, mx, ends + count, room, &s_new,
-                 L, 0);
+    __syncthreads();
+    const uint64_t nw = s_new;
+    if (t == 0) {
+        st->count = count + nw;
+        if (!(s_ncand > cand_cap || s_ncand >= 0xffffffffull)) st->carry = nw ? ends[count + nw - 1] : carry;
+        st->seg_cnt[seg + 1] = count + nw;
+    }
+    // The segment's longest chunks (at most klong) get lone lanes in
+    // k_hash_seg: histogram of sizes in 128 bands of (max+1)/128 bytes, the
+    // lowest band from which the bands above hold at most klong chunks.
+    const uint64_t hi = min(count + nw, cap);
+    const uint64_t start0 = st->start0;
+    for (uint64_t i = count + t; i < hi; i += kSelThreads) {
+        const uint64_t a = i ? ends[i - 1] : start0;
+        const uint64_t q = (ends[i] - a) * 128 / (mx + 1);
+        const uint32_t band = q < 127 ? (uint32_t)q : 127u;
+        atomicAdd(&hist[band], 1u);
+    }
     __syncthreads();
     if (t == 0) {
-        const uint64_t nw = s_new;
-        st->count = count + nw;
-        st->carry = nw ? ends[count + nw - 1] : carry;
-        st->seg_cnt[seg + 1] = count + nw;
+        uint32_t cum = 0;
+        int b = 128;
+        while (b > 0 && cum + hist[b - 1] <= klong) cum += hist[--b];
+        s_thr = b == 128 ? ~0ull : (b * (mx + 1) + 127) / 128;
+    }
+    __syncthreads();
+    const uint64_t thr = s_thr;
+    for (uint64_t i = count + t; i < hi; i += kSelThreads) {
+        const uint64_t a = i ? ends[i - 1] : start0;
+        if (ends[i] - a >= thr) {
+            const uint32_t k = atomicAdd(&s_nlong, 1u);
+            if (k < klong) long_idx[(size_t)seg * kLongMax + k] = (uint32_t)(i - count);
+        }
+    }
+    __syncthreads();
+    if (t == 0) {
+        st->thr[seg] = thr;
+        st->nlong[seg] = min(s_nlong, klong);
     }
 }
 
-// Digests of the chunks one segment's selection finalized.
+// Digests of the chunks one segment's selection finalized. The first
+// ceil(klong/4) CTAs give each of the segment's listed longest chunks a warp
+// of its own (lane 0); the other CTAs take one chunk per thread and skip
+// those.
 template <class H>
 __global__ void __launch_bounds__(128) k_hash_seg(const uint8_t *__restrict__ in,
                                                   const uint64_t *__restrict__ ends,
                                                   const PipeState *st, int seg,
-                                                  uint8_t *__restrict__ out) {
+                                                  const uint32_t *__restrict__ long_idx,
+                                                  uint32_t klong, uint8_t *__restrict__ out) {
     const uint64_t lo = st->seg_cnt[seg], hi = st->seg_cnt[seg + 1];
-    const uint64_t i = lo + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= hi) return;
+    const uint32_t long_ctas = (klong + 3) / 4;
+    uint64_t i;
+    if (blockIdx.x < long_ctas) {
+        const uint32_t w = blockIdx.x * 4 + threadIdx.x / 32;
+        if ((threadIdx.x & 31) != 0 || w >= st->nlong[seg]) return;
+        i = lo + long_idx[(size_t)seg * kLongMax + w];
+    } else {
+        i = lo + (uint64_t)(blockIdx.x - long_ctas) * blockDim.x + threadIdx.x;
+        if (i >= hi) return;
+        const uint64_t a0 = i ? ends[i - 1] : st->start0;
+        if (ends[i] - a0 >= st->thr[seg]) return;          // on a lone lane
+    }
     const uint64_t a = i ? ends[i - 1] : st->start0, b = ends[i];
     H hs;
     hash_range(in + a, b - a, hs);
@@ -454,14 +501,17 @@ int launch_pipe_segment(const uint8_t *d_in, uint64_t n, uint64_t n_sel, const h
     k_compact<<<ntiles, kWinThreads, 0, s_sel>>>(b.bitmap, (n + 31) / 32, b.tile_cnt, b.tile_off,
                                                  b.cands, b.cand_cap, tile0);
     k_select_seg<<<1, kSelThreads, 0, s_sel>>>(b.cands, b.cand_cap, b.bitmap, n_sel, L, p.min_chunk,
-                                               p.max_chunk, b.ends, b.cap, b.st, seg);
+                                               p.max_chunk, b.ends, b.cap, b.st, seg, b.long_idx,
+                                               b.klong);
     cudaEventRecord(ev_sel, s_sel);
     cudaStreamWaitEvent(s_hash, ev_sel, 0);
-    const unsigned grid = (unsigned)((max_chunks + 127) / 128);
+    const unsigned grid = (unsigned)((max_chunks + 127) / 128 + (b.klong + 3) / 4);
     if (algo == HG_MD5)
-        k_hash_seg<Md5Chain><<<grid, 128, 0, s_hash>>>(d_in, b.ends, b.st, seg, b.digests);
+        k_hash_seg<Md5Chain><<<grid, 128, 0, s_hash>>>(d_in, b.ends, b.st, seg, b.long_idx, b.klong,
+                                                       b.digests);
     else
-        k_hash_seg<Sha1><<<grid, 128, 0, s_hash>>>(d_in, b.ends, b.st, seg, b.digests);
+        k_hash_seg<Sha1><<<grid, 128, 0, s_hash>>>(d_in, b.ends, b.st, seg, b.long_idx, b.klong,
+                                                   b.digests);
     return cuda_status(cudaGetLastError());
 }
 

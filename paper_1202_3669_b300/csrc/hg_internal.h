@@ -84,7 +84,19 @@ struct PipeState {
     uint64_t ncand;      // candidates found so far
     uint64_t start0;     // start of the first chunk (0 for a whole buffer)
     uint64_t seg_cnt[kMaxSeg + 1];   // chunks finalized after segment k-1 (seg_cnt[0] = 0)
+    uint64_t thr[kMaxSeg];           // segment k: chunks at least this long run on lone lanes
+    uint32_t nlong[kMaxSeg];         // segment k: how many (listed in the long lists)
 };
+// Longest chunks of a segment given a warp of their own (one lane active):
+// a lone chain measured about 15-20 cycles per MD5 step against 27 when 32
+// chains share a warp, and the longest chain is the step's tail. At most one
+// such warp per scheduler (4 per SM, capped at kLongMax).
+constexpr uint32_t kLongMax = 1024;
+constexpr size_t kLongListBytes = (size_t)kMaxSeg * kLongMax * sizeof(uint32_t);
+inline uint32_t long_chains(int num_sms) {
+    const uint32_t k = 4u * (uint32_t)(num_sms > 0 ? num_sms : 1);
+    return k < kLongMax ? k : kLongMax;
+}
 struct PipeBufs {
     uint32_t *bitmap, *tile_cnt;
     uint64_t *tile_off, *cands, cand_cap;
@@ -92,6 +104,8 @@ struct PipeBufs {
     uint8_t *digests;
     PipeState *st;
     int *err;
+    uint32_t *long_idx;   // kMaxSeg lists of kLongMax chunk indexes (relative to the segment)
+    uint32_t klong;       // lone-lane chains per segment (<= kLongMax)
 };
 
 // hg_cdc.cu

@@ -108,7 +108,7 @@ int hg_stream_open(hg_ctx *ctx, int algo, const hg_cdc_params *p, uint64_t max_f
     st->end_cap = st->buf_cap / p->min_chunk + 2;
     const size_t sizes[] = {st->buf_cap, st->buf_cap, st->ntiles_cap * kWinThreads * 4,
                             st->ntiles_cap * 4, (st->ntiles_cap + 1) * 8, st->cand_cap * 8,
-                            st->end_cap * 8, sizeof(PipeState), 64, 64};
+                            st->end_cap * 8, sizeof(PipeState), 64, 64, kLongListBytes};
     size_t total = 0;
     for (size_t z : sizes) total += a256(z);
     st->mem_bytes = total;
@@ -141,6 +141,8 @@ int hg_stream_open(hg_ctx *ctx, int algo, const hg_cdc_params *p, uint64_t max_f
         st->pb.st = (PipeState *)take(sizes[7]);
         st->pb.err = (int *)take(sizes[8]);
         st->d_info = (uint64_t *)take(sizes[9]);
+        st->pb.long_idx = (uint32_t *)take(sizes[10]);
+        st->pb.klong = long_chains(ctx->num_sms);
         if (cudaMemset(st->pb.err, 0, 4) != cudaSuccess) rc = HG_ECUDA;
     }
     cudaSetDevice(prev);
