@@ -298,3 +298,20 @@ def test_config_cdc_1gib(hg, dist):
     for i in sorted(rng.integers(0, k, 300).tolist()) + [0, k - 1]:
         s = int(want[i - 1]) if i else 0
         assert dgn[i].tobytes() == hashlib.md5(data[s:int(want[i])].tobytes()).digest(), i
+
+
+@pytest.mark.parametrize("algo", [oracle.MD5, oracle.SHA1])
+def test_cdc_hash_all_chunks_at_max(hg, algo):
+    """Constant input: every chunk is cut at max, more of them than lone-lane warps
+    (the longest-chunk list stays empty) and, on a short input, fewer (all listed)."""
+    for v in range(256):
+        if oracle.window_candidates(bytes([v]) * 20, 20, 13, 0x0F0F).size == 0:
+            break
+    for n in (100 << 20, (3 << 20) + 17):
+        data = np.full(n, v, np.uint8)
+        ends, cnt, dg = hg.cdc_hash(to_device(data), algo)
+        hg.sync()
+        k = int(cnt.item())
+        want = np.array(list(range(65536, n, 65536)) + [n], np.uint64)
+        assert np.array_equal(ends[:k].cpu().numpy().astype(np.uint64), want)
+        assert np.array_equal(dg[:k].cpu().numpy(), oracle.hash_chunks(algo, data, want))
