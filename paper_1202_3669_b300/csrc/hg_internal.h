@@ -89,9 +89,10 @@ struct PipeState {
 };
 // Longest chunks of a segment given a warp of their own (one lane active):
 // a lone chain measured about 15-20 cycles per MD5 step against 27 when 32
-// chains share a warp, and the longest chain is the step's tail. One such
-// warp per SM per call (two concurrent 64 MiB calls: 63.1 GB/s against 60.8
-// with four per SM, which crowds the schedulers), capped at kLongMax.
+// chains share a warp, and the longest chain is the step's tail. As many
+// such warps per call as SMs (two concurrent 64 MiB calls: 63.1 GB/s against
+// 60.8 with four times as many, which crowds the schedulers), capped at
+// kLongMax.
 constexpr uint32_t kLongMax = 1024;
 constexpr size_t kLongListBytes = (size_t)kMaxSeg * kLongMax * sizeof(uint32_t);
 inline uint32_t long_chains(int num_sms) {
