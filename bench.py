@@ -64,7 +64,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the direct/batch/serve/CPU legs")
-    ap.add_argument("--leg", default=None, choices=["direct", "batch", "serve", "rabin", "blockmap"],
+    ap.add_argument("--leg", default=None,
+                    choices=["direct", "batch", "serve", "rabin", "blockmap", "configs"],
                     help="run only this extra leg (for profiling) and print its result")
     ap.add_argument("--batch-files", type=int, default=4096,
                     help="batch leg: use only the first N files of the 4096-file workload")
@@ -189,7 +190,18 @@ def cpu_baseline(versions, budget_s: float = 12.0):
         oracle.hash_chunks(oracle.MD5, s, e, L=L)
         total += s.size
     dt = time.perf_counter() - t0
+    # the same oracle on one thread, on a smaller sample (about a quarter of the budget)
+    n1 = int(min(versions[0].size, max(1 << 18, rate / nthreads * budget_s / 8)))
+    t1 = time.perf_counter()
+    for v in versions:
+        s1 = v[:n1]
+        e = oracle.cdc(s1, nthreads=1, L=L)
+        oracle.hash_chunks(oracle.MD5, s1, e, L=L)
+    dt1 = time.perf_counter() - t1
+    single = {"value": 2 * n1 / dt1 / 1e9, "unit": UNIT, "cores": 1, "seconds": dt1,
+              "sample": f"first {n1} bytes of each version"}
     return {"value": total / dt / 1e9, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+            "single_thread": single,
             "sample": f"first {nbytes} bytes of each of the two versions ({total} bytes), "
                       f"window candidates on {nthreads} threads + selection + per-chunk MD5",
             "seconds": dt}
@@ -263,6 +275,8 @@ def main():
             res = rabin_leg(hgb, dev, flush)
         elif args.leg == "blockmap":
             res = blockmap_leg(hgb, ctx, dev, flush)
+        elif args.leg == "configs":
+            res = configs_leg(hgb, ctx, dev, flush)
         else:
             res = serve_leg(hgb, ctx, batch_leg(hgb, ctx, dev, flush)["batched_graph_GBps"])
         print(json.dumps({"leg": args.leg, "result": res}), flush=True)
@@ -449,6 +463,7 @@ def main():
         extras["direct"] = direct_leg(hgb, ctxs[0], dev, flush)
         extras["rabin"] = rabin_leg(hgb, dev, flush)
         extras["blockmap"] = blockmap_leg(hgb, ctxs[0], dev, flush)
+        extras["configs"] = configs_leg(hgb, ctxs[0], dev, flush)
         extras["batch"] = batch_leg(hgb, ctxs[0], dev, flush)
         extras["serve"] = serve_leg(hgb, ctxs[0], extras["batch"]["batched_graph_GBps"])
         extras["cpu_baseline"] = cpu_baseline(versions)
@@ -478,7 +493,7 @@ def main():
                "step_ms_p50": statistics.median(step_ms), "step_ms_max": max(step_ms),
                "unpipelined": {"GBps": nbytes / (t_two / 1e3) / 1e9, "ms_per_step": t_two,
                                "calls": "hg_cdc_boundaries + hg_hash_chunks"}}
-        for k in ("direct", "rabin", "blockmap", "batch", "serve"):
+        for k in ("direct", "configs", "rabin", "blockmap", "batch", "serve"):
             if k in extras:
                 out[k] = extras[k]
         print(json.dumps(out), flush=True)
@@ -528,6 +543,97 @@ def direct_leg(hgb, ctx, dev, flush):
     ctx.sync()
     res["note"] = (f"1 GiB uniform bytes (seed 4); 262144 / 16384 / 1024 blocks; two-level = "
                    f"H(4 KiB segment digests) per 1 MiB block; HBM peak {peaks['hbm_gbs']} GB/s ({kind})")
+    return res
+
+
+def configs_leg(hgb, ctx, dev, flush):
+    """The other measured configurations: 8 MiB / 4 KiB blocks in one call (digests + hash-of-
+    hashes, MD5 and SHA-1), and 1 GiB chunking (uniform seed 4, text-like seed 5) kernel-only
+    and end to end from a pinned host buffer, plus 1 GiB fixed-block digests end to end (host
+    pieces copied on two streams, each piece hashed as it lands). Median of the timed runs,
+    L2 flushed before each."""
+    import torch
+    from gen import inputs as G
+    s = torch.cuda.current_stream(dev)
+
+    def med(fn, reps=10, warm=2):
+        ts = []
+        for i in range(reps + warm):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            fn()
+            b.record(s)
+            if i >= warm:
+                ts.append((a, b))
+        torch.cuda.synchronize()
+        return statistics.median(a.elapsed_time(b) for a, b in ts) / 1e3
+
+    res = {}
+    c1 = torch.from_numpy(G.uniform_bytes(8 << 20, seed=1)).to(dev)
+    for algo, name in ((hgb.MD5, "md5"), (hgb.SHA1, "sha1")):
+        dl = 16 if algo == hgb.MD5 else 20
+        out = torch.empty((2048, dl), dtype=torch.uint8, device=dev)
+        rt = torch.empty(dl, dtype=torch.uint8, device=dev)
+        t = med(lambda: ctx.hash_blocks(c1, 4096, algo, root=True, out=out, root_out=rt))
+        res[f"c1_8MiB_4KiB_{name}_with_root"] = {"ms": t * 1e3, "GBps": (8 << 20) / t / 1e9}
+    del c1
+    n = 1 << 30
+    d = torch.empty(n, dtype=torch.uint8, device=dev)
+    cap = n // 2048 + 2
+    outs = (torch.empty(cap, dtype=torch.int64, device=dev), torch.zeros(1, dtype=torch.int64, device=dev),
+            torch.empty((cap, 16), dtype=torch.uint8, device=dev))
+    h_ends = torch.empty(cap, dtype=torch.int64).pin_memory()
+    h_dg = torch.empty((cap, 16), dtype=torch.uint8).pin_memory()
+    h_cnt = torch.empty(1, dtype=torch.int64).pin_memory()
+    p = hgb.default_params()
+    for dist, gen in (("uniform", lambda: G.uniform_bytes(n, seed=4)),
+                      ("text", lambda: G.text_like_bytes(n, seed=5))):
+        host = torch.from_numpy(gen()).pin_memory()
+        d.copy_(host)
+        t_k = med(lambda: ctx.cdc_hash(d, hgb.MD5, p, out=outs, stream=s))
+
+        def e2e():
+            ctx.cdc_hash_from_host(host, d, hgb.MD5, p, out=outs, stream=s)
+            h_cnt.copy_(outs[1], non_blocking=True)
+            h_ends.copy_(outs[0], non_blocking=True)
+            h_dg.copy_(outs[2], non_blocking=True)
+        t_e = med(e2e, reps=5)
+        ctx.sync()
+        res[f"c3_1GiB_{dist}_cdc_md5"] = {"kernel_GBps": n / t_k / 1e9, "kernel_ms": t_k * 1e3,
+                                           "e2e_GBps": n / t_e / 1e9, "e2e_ms": t_e * 1e3,
+                                           "chunks": int(outs[1].item())}
+        if dist == "uniform":
+            streams = [torch.cuda.Stream(dev) for _ in range(2)]
+            piece = 64 << 20
+            for algo, name in ((hgb.MD5, "md5"), (hgb.SHA1, "sha1")):
+                dl = 16 if algo == hgb.MD5 else 20
+                dg = torch.empty((n // 4096, dl), dtype=torch.uint8, device=dev)
+                h_out = torch.empty((n // 4096, dl), dtype=torch.uint8).pin_memory()
+
+                def blocks_e2e():
+                    ev0 = torch.cuda.Event()
+                    ev0.record(s)
+                    for k in range(n // piece):
+                        st = streams[k % 2]
+                        st.wait_event(ev0)
+                        with torch.cuda.stream(st):
+                            d[k * piece:(k + 1) * piece].copy_(host[k * piece:(k + 1) * piece],
+                                                              non_blocking=True)
+                            seg = dg[k * piece // 4096:(k + 1) * piece // 4096]
+                            ctx.hash_blocks(d[k * piece:(k + 1) * piece], 4096, algo, root=False,
+                                            out=seg, stream=st)
+                            h_out[k * piece // 4096:(k + 1) * piece // 4096].copy_(seg, non_blocking=True)
+                    for st in streams:
+                        s.wait_stream(st)
+                t_b = med(blocks_e2e, reps=5)
+                res[f"c3_1GiB_uniform_4KiB_{name}_e2e"] = {"GBps": n / t_b / 1e9, "ms": t_b * 1e3}
+        del host
+    ctx.sync()
+    res["note"] = ("c1: one hg_hash_blocks call with the root (latency-bound: 2048 chains + one "
+                   "serial root); c3: hg_cdc_hash on device input vs hg_cdc_hash_h2d from pinned "
+                   "host memory (+ D2H of ends and digests); fixed-block e2e: 64 MiB pieces copied and "
+                   "hashed on two streams, digests copied back (root not included)")
     return res
 
 

@@ -142,6 +142,7 @@ int hg_destroy(hg_ctx *c) {
     cudaFree(c->d_tile_off);
     cudaFree(c->d_cands);
     cudaFree(c->d_segdig);
+    cudaFree(c->d_tasks);
     cudaFree(c->d_err);
     if (c->pipe_ready) {
         if (c->p_exec) cudaGraphExecDestroy(c->p_exec);
@@ -369,7 +370,12 @@ static int enqueue_cdc_hash(hg_ctx *c, int algo, const uint8_t *d_in, uint64_t n
     PipeBufs pb{c->d_bitmap, c->d_tile_cnt, c->d_tile_off, c->d_cands, c->cand_cap,
                 d_ends, cap, d_digests, (PipeState *)c->d_pipe, c->d_err,
                 reinterpret_cast<uint32_t *>(static_cast<char *>(c->d_pipe) + sizeof(PipeState)),
-                long_chains(c->num_sms)};
+                long_chains(c->num_sms), c->d_tasks};
+    // Device input in several segments: digests after the last selection, in
+    // one length-sorted launch. Per-segment digest launches shared the SMs with
+    // the later segments' window kernels (1 GiB: 14.6 ms against 10.8 ms of
+    // windows). Host input keeps per-segment digests, which overlap the copies.
+    const bool defer = !h_in && nseg > 1;
     int r;
     cudaEventRecord(c->p_fork, s);
     cudaStreamWaitEvent(c->p_win, c->p_fork, 0);
@@ -393,10 +399,12 @@ static int enqueue_cdc_hash(hg_ctx *c, int algo, const uint8_t *d_in, uint64_t n
         const uint64_t L = (k == nseg - 1) ? n : hi;
         const uint64_t max_chunks = (hi - lo + p->max_chunk) / p->min_chunk + 2;
         if ((r = launch_pipe_segment(d_in, n, n, *p, algo, t0, nt, L, k, max_chunks, pb, c->p_win,
-                                     c->p_sel, c->p_hash[k], c->p_ev_win[k], c->p_ev_sel[k],
-                                     h_in ? c->p_ev_copy[k] : nullptr)))
+                                     c->p_sel, defer ? nullptr : c->p_hash[k], c->p_ev_win[k],
+                                     c->p_ev_sel[k], h_in ? c->p_ev_copy[k] : nullptr)))
             return r;
     }
+    if (defer && (r = launch_hash_sorted(d_in, n / p->min_chunk + 2, *p, algo, pb, c->p_sel)))
+        return r;
     cudaEventRecord(c->p_done_sel, c->p_sel);
     cudaStreamWaitEvent(s, c->p_done_sel, 0);
     cudaEventRecord(c->p_done_sel, c->p_win);
@@ -433,7 +441,9 @@ static int run_cdc_hash(hg_ctx *c, int algo, const uint8_t *h_in, const uint8_t 
     if (!d_in || !d_ends || !d_digests || (reinterpret_cast<uintptr_t>(d_digests) & 3))
         return HG_EINVAL;
     if (cap < n / p->min_chunk + 1) return HG_ECAPACITY;
-    if ((r = ensure_cdc(c, n)) || (r = pipe_setup(c))) return r;
+    if ((r = ensure_cdc(c, n)) || (r = pipe_setup(c)) ||
+        (r = ensure(c, (void **)&c->d_tasks, &c->tasks_cap, n / p->min_chunk + 2, 4)))
+        return r;
     // With host input the launches go straight onto the context streams, so the
     // segment copies use the process-wide copy stream and several calls' copies
     // queue instead of interleaving (a replayed graph would pick its own

@@ -364,6 +364,82 @@ __global__ void __launch_bounds__(128) k_hash_seg(const uint8_t *__restrict__ in
     store_digest(hs, out + i * H::kDigest);
 }
 
+// Deferred digests (launch_hash_sorted): length bands of (max+1)/128 bytes,
+// numbered longest first.
+__device__ __forceinline__ uint32_t len_band(uint64_t len, uint64_t mx) {
+    const uint64_t q = len * 128 / (mx + 1);
+    return 127u - (q < 127 ? (uint32_t)q : 127u);
+}
+
+__global__ void __launch_bounds__(256) k_len_hist(const uint64_t *__restrict__ ends, PipeState *st,
+                                                  uint64_t mx) {
+    __shared__ uint32_t h[128];
+    if (threadIdx.x < 128) h[threadIdx.x] = 0;
+    __syncthreads();
+    const uint64_t cnt = st->count, s0 = st->start0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t a = i ? ends[i - 1] : s0;
+        atomicAdd(&h[len_band(ends[i] - a, mx)], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < 128 && h[threadIdx.x]) atomicAdd(&st->band_cnt[threadIdx.x], h[threadIdx.x]);
+}
+
+// One warp: exclusive scan of the 128 band counts into the bands' first slots.
+__global__ void k_len_scan(PipeState *st) {
+    const int lane = threadIdx.x;
+    uint32_t v[4], sum = 0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) { v[k] = st->band_cnt[4 * lane + k]; sum += v[k]; }
+    uint32_t x = sum;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+    }
+    uint32_t run = x - sum;
+#pragma unroll
+    for (int k = 0; k < 4; k++) { st->band_cur[4 * lane + k] = run; run += v[k]; }
+}
+
+__global__ void __launch_bounds__(256) k_len_scatter(const uint64_t *__restrict__ ends, PipeState *st,
+                                                     uint64_t mx, uint32_t *__restrict__ tasks) {
+    const uint64_t cnt = st->count, s0 = st->start0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t a = i ? ends[i - 1] : s0;
+        const uint32_t at = atomicAdd(&st->band_cur[len_band(ends[i] - a, mx)], 1u);
+        tasks[at] = (uint32_t)i;
+    }
+}
+
+// Warps 0..klong-1 take the klong longest chunks on lane 0; the next warps take
+// the rest 32 at a time, longest first (CTAs start in index order).
+template <class H>
+__global__ void __launch_bounds__(128) k_hash_sorted(const uint8_t *__restrict__ in,
+                                                     const uint64_t *__restrict__ ends,
+                                                     const PipeState *st,
+                                                     const uint32_t *__restrict__ tasks,
+                                                     uint32_t klong, uint8_t *__restrict__ out) {
+    const uint64_t cnt = st->count;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const uint32_t lane = threadIdx.x & 31;
+    uint64_t k;
+    if (warp < klong) {
+        if (lane) return;
+        k = warp;
+    } else {
+        k = klong + (warp - klong) * 32 + lane;
+    }
+    if (k >= cnt) return;
+    const uint64_t i = tasks[k];
+    const uint64_t a = i ? ends[i - 1] : st->start0, b = ends[i];
+    H hs;
+    hash_range(in + a, b - a, hs);
+    store_digest(hs, out + i * H::kDigest);
+}
+
 // Streaming: start a feed whose first chunk starts at start0 of the buffer.
 __global__ void k_stream_init(PipeState *st, uint64_t start0) {
     if (threadIdx.x == 0) {
@@ -504,6 +580,7 @@ int launch_pipe_segment(const uint8_t *d_in, uint64_t n, uint64_t n_sel, const h
                                                p.max_chunk, b.ends, b.cap, b.st, seg, b.long_idx,
                                                b.klong);
     cudaEventRecord(ev_sel, s_sel);
+    if (!s_hash) return cuda_status(cudaGetLastError());
     cudaStreamWaitEvent(s_hash, ev_sel, 0);
     const unsigned grid = (unsigned)((max_chunks + 127) / 128 + (b.klong + 3) / 4);
     if (algo == HG_MD5)
@@ -512,6 +589,21 @@ int launch_pipe_segment(const uint8_t *d_in, uint64_t n, uint64_t n_sel, const h
     else
         k_hash_seg<Sha1><<<grid, 128, 0, s_hash>>>(d_in, b.ends, b.st, seg, b.long_idx, b.klong,
                                                    b.digests);
+    return cuda_status(cudaGetLastError());
+}
+
+int launch_hash_sorted(const uint8_t *d_in, uint64_t max_chunks, const hg_cdc_params &p, int algo,
+                       const PipeBufs &b, cudaStream_t s) {
+    const unsigned sgrid = 4 * 148;
+    k_len_hist<<<sgrid, 256, 0, s>>>(b.ends, b.st, p.max_chunk);
+    k_len_scan<<<1, 32, 0, s>>>(b.st);
+    k_len_scatter<<<sgrid, 256, 0, s>>>(b.ends, b.st, p.max_chunk, b.tasks);
+    const uint64_t warps = b.klong + (max_chunks + 31) / 32;
+    const unsigned grid = (unsigned)((warps * 32 + 127) / 128);
+    if (algo == HG_MD5)
+        k_hash_sorted<Md5Chain><<<grid, 128, 0, s>>>(d_in, b.ends, b.st, b.tasks, b.klong, b.digests);
+    else
+        k_hash_sorted<Sha1><<<grid, 128, 0, s>>>(d_in, b.ends, b.st, b.tasks, b.klong, b.digests);
     return cuda_status(cudaGetLastError());
 }
 

@@ -20,6 +20,7 @@ struct hg_ctx {
     uint64_t *d_cands = nullptr;     uint64_t cand_cap = 0;
     uint64_t *d_ncand = nullptr;     // one word
     uint8_t *d_segdig = nullptr;     uint64_t segdig_cap = 0;   // two-level segment digests
+    uint32_t *d_tasks = nullptr;     uint64_t tasks_cap = 0;    // sorted chunk-digest tasks
     // pipelined chunking (hg_cdc_hash): streams, events, device state
     bool pipe_ready = false;
     cudaStream_t p_win = nullptr, p_sel = nullptr, p_hash[64] = {};
@@ -86,6 +87,8 @@ struct PipeState {
     uint64_t seg_cnt[kMaxSeg + 1];   // chunks finalized after segment k-1 (seg_cnt[0] = 0)
     uint64_t thr[kMaxSeg];           // segment k: chunks at least this long run on lone lanes
     uint32_t nlong[kMaxSeg];         // segment k: how many (listed in the long lists)
+    uint32_t band_cnt[128];          // deferred digests: chunks per length band (longest first)
+    uint32_t band_cur[128];          // and the bands' next free task slots
 };
 // Longest chunks of a segment given a warp of their own (one lane active):
 // a lone chain measured about 15-20 cycles per MD5 step against 27 when 32
@@ -108,6 +111,7 @@ struct PipeBufs {
     int *err;
     uint32_t *long_idx;   // kMaxSeg lists of kLongMax chunk indexes (relative to the segment)
     uint32_t klong;       // lone-lane chains per segment (<= kLongMax)
+    uint32_t *tasks;      // deferred digests: chunk indexes sorted by length (cap entries)
 };
 
 // hg_cdc.cu
@@ -128,6 +132,14 @@ int launch_window_rabin_range(const uint8_t *d_in, uint64_t n, const hg_cdc_para
                               uint64_t ntiles, cudaStream_t s);
 // n: bytes in d_in; n_sel: end of the stream for selection (n, or ~0 when the
 // stream continues beyond d_in).
+// Digests of all chunks a pipeline decided, after its last selection, in one
+// launch: chunks counting-sorted by length (longest first), the longest klong
+// on lone lanes, the rest 32 to a warp in that order. Used when a buffer has
+// several segments, where per-segment digest launches would share the SMs
+// with the later segments' window kernels.
+int launch_hash_sorted(const uint8_t *d_in, uint64_t max_chunks, const hg_cdc_params &p, int algo,
+                       const PipeBufs &b, cudaStream_t s);
+// s_hash == nullptr: the segment's digests are left to launch_hash_sorted.
 int launch_pipe_segment(const uint8_t *d_in, uint64_t n, uint64_t n_sel, const hg_cdc_params &p,
                         int algo, uint32_t tile0, uint32_t ntiles, uint64_t L, int seg,
                         uint64_t max_chunks, const PipeBufs &b, cudaStream_t s_win,
