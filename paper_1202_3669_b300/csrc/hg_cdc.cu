@@ -414,30 +414,46 @@ __global__ void __launch_bounds__(256) k_len_scatter(const uint64_t *__restrict_
     }
 }
 
-// Warps 0..klong-1 take the klong longest chunks on lane 0; the next warps take
-// the rest 32 at a time, longest first (CTAs start in index order).
+// The first ceil(klong/4) CTAs give the klong longest chunks a warp each
+// (lane 0); the other CTAs are persistent bulk warps that take the rest 32 at
+// a time, longest first, from a counter. Few bulk warps per SM leave issue
+// slots to the long chains, which set the launch's duration: with every
+// chunk's warp resident at once (1 GiB: 3.3K warps) the long chains crawled.
+// Measured on 1 GiB (105K chunks): one bulk CTA of 4 warps per SM 12.42 ms
+// for the whole call, two 12.65, four 13.05, one warp per chunk 12.66.
 template <class H>
 __global__ void __launch_bounds__(128) k_hash_sorted(const uint8_t *__restrict__ in,
                                                      const uint64_t *__restrict__ ends,
-                                                     const PipeState *st,
+                                                     PipeState *st,
                                                      const uint32_t *__restrict__ tasks,
                                                      uint32_t klong, uint8_t *__restrict__ out) {
-    const uint64_t cnt = st->count;
-    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const uint64_t cnt = st->count, s0 = st->start0;
     const uint32_t lane = threadIdx.x & 31;
-    uint64_t k;
-    if (warp < klong) {
-        if (lane) return;
-        k = warp;
-    } else {
-        k = klong + (warp - klong) * 32 + lane;
+    const uint32_t long_ctas = (klong + 3) / 4;
+    if (blockIdx.x < long_ctas) {
+        const uint64_t k = (uint64_t)blockIdx.x * 4 + threadIdx.x / 32;
+        if (lane || k >= klong || k >= cnt) return;
+        const uint64_t i = tasks[k];
+        const uint64_t a = i ? ends[i - 1] : s0;
+        H hs;
+        hash_range(in + a, ends[i] - a, hs);
+        store_digest(hs, out + i * H::kDigest);
+        return;
     }
-    if (k >= cnt) return;
-    const uint64_t i = tasks[k];
-    const uint64_t a = i ? ends[i - 1] : st->start0, b = ends[i];
-    H hs;
-    hash_range(in + a, b - a, hs);
-    store_digest(hs, out + i * H::kDigest);
+    while (true) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&st->task_ctr, 32ull);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (klong + base >= cnt) return;
+        const uint64_t k = klong + base + lane;
+        if (k < cnt) {
+            const uint64_t i = tasks[k];
+            const uint64_t a = i ? ends[i - 1] : s0;
+            H hs;
+            hash_range(in + a, ends[i] - a, hs);
+            store_digest(hs, out + i * H::kDigest);
+        }
+    }
 }
 
 // Streaming: start a feed whose first chunk starts at start0 of the buffer.
@@ -592,14 +608,18 @@ int launch_pipe_segment(const uint8_t *d_in, uint64_t n, uint64_t n_sel, const h
     return cuda_status(cudaGetLastError());
 }
 
+constexpr uint64_t kBulkCtasPerSm = 1;
+
 int launch_hash_sorted(const uint8_t *d_in, uint64_t max_chunks, const hg_cdc_params &p, int algo,
                        const PipeBufs &b, cudaStream_t s) {
     const unsigned sgrid = 4 * 148;
     k_len_hist<<<sgrid, 256, 0, s>>>(b.ends, b.st, p.max_chunk);
     k_len_scan<<<1, 32, 0, s>>>(b.st);
     k_len_scatter<<<sgrid, 256, 0, s>>>(b.ends, b.st, p.max_chunk, b.tasks);
-    const uint64_t warps = b.klong + (max_chunks + 31) / 32;
-    const unsigned grid = (unsigned)((warps * 32 + 127) / 128);
+    // bulk: kBulkCtasPerSm CTAs of 4 warps per SM (the lone-warp count is one per SM)
+    const uint64_t bulk_ctas = (uint64_t)b.klong * kBulkCtasPerSm;
+    const uint64_t need = ((max_chunks + 31) / 32 + 3) / 4;
+    const unsigned grid = (unsigned)((b.klong + 3) / 4 + (need < bulk_ctas ? need : bulk_ctas));
     if (algo == HG_MD5)
         k_hash_sorted<Md5Chain><<<grid, 128, 0, s>>>(d_in, b.ends, b.st, b.tasks, b.klong, b.digests);
     else

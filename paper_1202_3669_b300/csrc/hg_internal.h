@@ -89,6 +89,7 @@ struct PipeState {
     uint32_t nlong[kMaxSeg];         // segment k: how many (listed in the long lists)
     uint32_t band_cnt[128];          // deferred digests: chunks per length band (longest first)
     uint32_t band_cur[128];          // and the bands' next free task slots
+    unsigned long long task_ctr;     // deferred digests: next 32-task group for the bulk warps
 };
 // Longest chunks of a segment given a warp of their own (one lane active):
 // a lone chain measured about 15-20 cycles per MD5 step against 27 when 32
