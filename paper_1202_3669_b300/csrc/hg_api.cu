@@ -399,8 +399,8 @@ static int enqueue_cdc_hash(hg_ctx *c, int algo, const uint8_t *d_in, uint64_t n
         const uint64_t L = (k == nseg - 1) ? n : hi;
         const uint64_t max_chunks = (hi - lo + p->max_chunk) / p->min_chunk + 2;
         if ((r = launch_pipe_segment(d_in, n, n, *p, algo, t0, nt, L, k, max_chunks, pb, c->p_win,
-                                     c->p_sel, defer ? nullptr : c->p_hash[k], c->p_ev_win[k],
-                                     c->p_ev_sel[k], h_in ? c->p_ev_copy[k] : nullptr)))
+                                     c->p_sel, c->p_hash[k], c->p_ev_win[k], c->p_ev_sel[k],
+                                     h_in ? c->p_ev_copy[k] : nullptr, !defer)))
             return r;
     }
     if (defer && (r = launch_hash_sorted(d_in, n / p->min_chunk + 2, *p, algo, pb, c->p_sel)))

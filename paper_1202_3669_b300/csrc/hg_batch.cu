@@ -40,8 +40,8 @@ int hg_batch_create(hg_ctx *ctx, const uint64_t *h_file_off, uint32_t nfile,
                     const hg_cdc_params *p, hg_batch **out) {
     if (!ctx || !h_file_off || !p || !out || nfile == 0 || nfile >= (1u << 31)) return HG_EINVAL;
     *out = nullptr;
-    if (p->window_hash == HG_WIN_RABIN) return HG_EUNSUPPORTED;
-    if (p->window_hash != HG_WIN_MD5 || p->window < 1 || p->window > 55 || p->mask_bits < 1 ||
+    if ((p->window_hash != HG_WIN_MD5 && p->window_hash != HG_WIN_RABIN) || p->window < 1 ||
+        p->window > (p->window_hash == HG_WIN_RABIN ? 64u : 55u) || p->mask_bits < 1 ||
         p->mask_bits > 32 ||
         (p->mask_bits < 32 && (p->magic >> p->mask_bits)) || p->min_chunk < 1 ||
         p->min_chunk > p->max_chunk)

@@ -579,7 +579,7 @@ int launch_pipe_segment(const uint8_t *d_in, uint64_t n, uint64_t n_sel, const h
                         int algo, uint32_t tile0, uint32_t ntiles, uint64_t L, int seg,
                         uint64_t max_chunks, const PipeBufs &b, cudaStream_t s_win,
                         cudaStream_t s_sel, cudaStream_t s_hash, cudaEvent_t ev_win,
-                        cudaEvent_t ev_sel, cudaEvent_t ev_input) {
+                        cudaEvent_t ev_sel, cudaEvent_t ev_input, bool digests) {
     if (ev_input) cudaStreamWaitEvent(s_win, ev_input, 0);    // this segment's bytes are in place
     // windows run back to back on s_win; the small serial steps (scan, compaction,
     // selection) of segment k run on s_sel, in segment order, once its windows are done
@@ -596,7 +596,7 @@ int launch_pipe_segment(const uint8_t *d_in, uint64_t n, uint64_t n_sel, const h
                                                p.max_chunk, b.ends, b.cap, b.st, seg, b.long_idx,
                                                b.klong);
     cudaEventRecord(ev_sel, s_sel);
-    if (!s_hash) return cuda_status(cudaGetLastError());
+    if (!digests) return cuda_status(cudaGetLastError());
     cudaStreamWaitEvent(s_hash, ev_sel, 0);
     const unsigned grid = (unsigned)((max_chunks + 127) / 128 + (b.klong + 3) / 4);
     if (algo == HG_MD5)

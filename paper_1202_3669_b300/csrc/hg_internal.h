@@ -140,12 +140,12 @@ int launch_window_rabin_range(const uint8_t *d_in, uint64_t n, const hg_cdc_para
 // with the later segments' window kernels.
 int launch_hash_sorted(const uint8_t *d_in, uint64_t max_chunks, const hg_cdc_params &p, int algo,
                        const PipeBufs &b, cudaStream_t s);
-// s_hash == nullptr: the segment's digests are left to launch_hash_sorted.
+// digests = false: the segment's digests are left to launch_hash_sorted.
 int launch_pipe_segment(const uint8_t *d_in, uint64_t n, uint64_t n_sel, const hg_cdc_params &p,
                         int algo, uint32_t tile0, uint32_t ntiles, uint64_t L, int seg,
                         uint64_t max_chunks, const PipeBufs &b, cudaStream_t s_win,
                         cudaStream_t s_sel, cudaStream_t s_hash, cudaEvent_t ev_win,
-                        cudaEvent_t ev_sel, cudaEvent_t ev_input);
+                        cudaEvent_t ev_sel, cudaEvent_t ev_input, bool digests = true);
 // streaming chunking (hg_stream.cu helpers in hg_cdc.cu)
 int launch_stream_init(PipeState *st, uint64_t start0, cudaStream_t s);
 int launch_stream_out(const uint64_t *ends, const PipeState *st, uint64_t base, uint64_t *d_ends_out,
@@ -211,6 +211,8 @@ size_t job_scratch_bytes(uint64_t ntiles, uint64_t cand_cap, uint64_t total_slot
 void job_scratch_carve(char *mem, uint64_t ntiles, uint64_t cand_cap, uint64_t total_slots,
                        JobScratch *sc);
 int job_window_occupancy(uint32_t window);
+// Shared-memory opt-in of the batch-job Rabin window kernels (current device).
+int job_rabin_prepare();
 int enqueue_cdc_job(const JobDev &j, const JobScratch &sc, const hg_cdc_params &p, int algo,
                     const JobTuning &tn, int num_sms, uint64_t *d_ends, uint64_t *d_counts,
                     uint8_t *d_digests, cudaStream_t s);

@@ -22,6 +22,7 @@
 
 #include "hg_device.cuh"
 #include "hg_internal.h"
+#include "hg_rabin.cuh"
 #include "hg_select.cuh"
 #include "hg_window.cuh"
 
@@ -318,6 +319,58 @@ __global__ void k_job_hash(JobDev j, const uint64_t *__restrict__ ends,
     }
 }
 
+// Rabin window over the batch's per-file tiles: persistent CTAs build the
+// fingerprint tables once, then take groups of 4 global tiles; each 64-thread
+// quarter handles one tile (128 window ends per thread) of whichever file
+// owns it, in the same bitmap layout and tile counts as k_job_window. Files
+// sit at any offset, so strips are realigned from 16-byte loads.
+template <int W>
+__global__ void __launch_bounds__(rabin::kThreads, 2)
+    k_job_rabin(JobDev j, uint32_t wrt, uint32_t mask, uint32_t magic, uint32_t *__restrict__ bitmap,
+                uint32_t *__restrict__ tile_cnt) {
+    using namespace rabin;
+    extern __shared__ __align__(16) uint32_t tabs[];
+    __shared__ uint32_t warp_cnt[kThreads / 32];
+    const uint32_t wlen = W ? (uint32_t)W : wrt;
+    const int t = threadIdx.x, lane = t & 31;
+    build_tables(tabs, wlen);
+    const uint32_t *T = tabs + lane;
+    const uint32_t *U = tabs + 256 * 32 + lane;
+    const uint64_t ngroups = ((uint64_t)j.ntiles + kTilesPerGroup - 1) / kTilesPerGroup;
+    const uint32_t sub = (uint32_t)t >> 6, q = (uint32_t)t & 63;
+    for (uint64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
+        const uint64_t tile = g * kTilesPerGroup + sub;
+        uint32_t bits[4] = {0, 0, 0, 0};
+        if (tile < j.ntiles) {
+            const uint32_t f = tile_file(j, (uint32_t)tile);
+            const uint64_t lo = (tile - j.tile_start[f]) * kWinTile;
+            strip_bits<W, true>(jptr(j, f), jlen(j, f), lo + (uint64_t)q * kStrip, wlen, mask, magic,
+                                T, U, bits);
+            uint4 *dst = reinterpret_cast<uint4 *>(bitmap + tile * kWinThreads) + q;
+            *dst = make_uint4(bits[0], bits[1], bits[2], bits[3]);
+        }
+        const uint32_t c = __reduce_add_sync(0xffffffffu, (uint32_t)(__popc(bits[0]) + __popc(bits[1]) +
+                                                                   __popc(bits[2]) + __popc(bits[3])));
+        if (lane == 0) warp_cnt[t >> 5] = c;
+        __syncthreads();
+        if (t < (int)kTilesPerGroup && g * kTilesPerGroup + t < j.ntiles)
+            tile_cnt[g * kTilesPerGroup + t] = warp_cnt[2 * t] + warp_cnt[2 * t + 1];
+        __syncthreads();
+    }
+}
+
+template <int W>
+cudaError_t job_rabin_opt_in() {
+    return cudaFuncSetAttribute(k_job_rabin<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)rabin::kSmem);
+}
+
+template <int W>
+void launch_job_rabin_t(int grid, const JobDev &j, uint32_t w, uint32_t mask, uint32_t magic,
+                        uint32_t *bm, uint32_t *tc, cudaStream_t s) {
+    k_job_rabin<W><<<grid, rabin::kThreads, rabin::kSmem, s>>>(j, w, mask, magic, bm, tc);
+}
+
 template <int W>
 void launch_job_window_t(int grid, const JobDev &j, uint32_t w, uint32_t mask, uint32_t magic,
                          uint32_t *bm, uint32_t *tc, unsigned long long *ctr, int *err,
@@ -333,6 +386,17 @@ int occupancy_t() {
 }
 
 }  // namespace
+
+int job_rabin_prepare() {
+    if (job_rabin_opt_in<0>() != cudaSuccess || job_rabin_opt_in<16>() != cudaSuccess ||
+        job_rabin_opt_in<20>() != cudaSuccess || job_rabin_opt_in<24>() != cudaSuccess ||
+        job_rabin_opt_in<32>() != cudaSuccess || job_rabin_opt_in<48>() != cudaSuccess ||
+        job_rabin_opt_in<64>() != cudaSuccess) {
+        cudaGetLastError();
+        return HG_ECUDA;
+    }
+    return HG_OK;
+}
 
 int job_window_occupancy(uint32_t w) {
     switch (w) {
@@ -397,7 +461,19 @@ int enqueue_cdc_job(const JobDev &j, const JobScratch &sc, const hg_cdc_params &
         const uint32_t mask = p.mask_bits >= 32 ? 0xffffffffu : ((1u << p.mask_bits) - 1u);
         const int grid = (int)std::min<uint64_t>(j.ntiles, (uint64_t)num_sms * tn.window_ctas);
         unsigned long long *ctr = sc.words + kJobTileCtr;
-        switch (p.window) {
+        if (p.window_hash == HG_WIN_RABIN) {
+            if (p.window < 1 || p.window > (uint32_t)rabin::kPre) return HG_EUNSUPPORTED;
+            const uint64_t groups = (j.ntiles + rabin::kTilesPerGroup - 1) / rabin::kTilesPerGroup;
+            const int rgrid = (int)std::min<uint64_t>(groups, (uint64_t)num_sms * 2);
+            switch (p.window) {
+#define HG_JR(w)                                                                                \
+    case w: launch_job_rabin_t<w>(rgrid, j, w, mask, p.magic, sc.bitmap, sc.tile_cnt, s); break;
+                HG_JR(16) HG_JR(20) HG_JR(24) HG_JR(32) HG_JR(48) HG_JR(64)
+#undef HG_JR
+                default:
+                    launch_job_rabin_t<0>(rgrid, j, p.window, mask, p.magic, sc.bitmap, sc.tile_cnt, s);
+            }
+        } else switch (p.window) {
 #define HG_JW(w)                                                                                \
     case w:                                                                                     \
         launch_job_window_t<w>(grid, j, w, mask, p.magic, sc.bitmap, sc.tile_cnt, ctr, sc.err, s); \

@@ -184,8 +184,8 @@ int hg_server_create(hg_ctx *ctx, const hg_server_config *cfg, hg_server **out) 
     if (!ctx || !cfg || !out) return HG_EINVAL;
     *out = nullptr;
     const hg_cdc_params &p = cfg->cdc;
-    if (p.window_hash == HG_WIN_RABIN) return HG_EUNSUPPORTED;
-    if (p.window_hash != HG_WIN_MD5 || p.window < 1 || p.window > 55 || p.mask_bits < 1 ||
+    if ((p.window_hash != HG_WIN_MD5 && p.window_hash != HG_WIN_RABIN) || p.window < 1 ||
+        p.window > (p.window_hash == HG_WIN_RABIN ? 64u : 55u) || p.mask_bits < 1 ||
         p.mask_bits > 32 ||
         (p.mask_bits < 32 && (p.magic >> p.mask_bits)) || p.min_chunk < 1 || p.min_chunk > p.max_chunk ||
         cfg->max_wave_bytes == 0 || cfg->max_wave_requests == 0 || cfg->max_inflight_waves == 0 ||

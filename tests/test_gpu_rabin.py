@@ -148,9 +148,57 @@ def test_config_rabin_1gib(hg):
         assert dgn[i].tobytes() == hashlib.md5(data[s:int(want[i])].tobytes()).digest(), i
 
 
-def test_batch_and_server_refuse_rabin(hg):
+@pytest.mark.parametrize("algo", [oracle.MD5, oracle.SHA1])
+@pytest.mark.parametrize("offset", [0, 5])
+def test_batch(hg, algo, offset):
+    """Batched Rabin chunking (per-file tiles, files at any offset) equals each file alone."""
     import paper_1202_3669_b300 as hgb
-    with pytest.raises(hgb.HashGPUError):
-        hgb.Batch(hg, np.array([0, 1000, 5000], np.uint64), P())
-    with pytest.raises(hgb.HashGPUError):
-        hgb.Server(hg, device_budget=256 << 20, max_wave_bytes=16 << 20, p=P())
+    sizes = np.array([0, 1, 47, 48, 49, 100, 2047, 8192, 8193, 70_000, 0, 300_000, (1 << 20) + 77,
+                      2_500_000, 65_537] + G.lognormal_sizes(120, seed=41, median=30_000, sigma=1.4,
+                                                           hi=3 << 20).tolist(), dtype=np.int64)
+    data, off = G.files_from_sizes(sizes, 42)
+    p = P()
+    b = hgb.Batch(hg, off, p)
+    out = b.cdc_hash(to_device(data, offset), algo, graph=bool(offset))
+    b.sync()
+    for f in range(len(sizes)):
+        body = data[off[f]:off[f + 1]]
+        want = oracle.cdc(body, 48, 13, 0x0F0F, 2048, 65536, nthreads=8, kind=R)
+        ends, dg = b.file_results(f, *out)
+        assert np.array_equal(ends, want), (f, sizes[f])
+        assert np.array_equal(dg, oracle.hash_chunks(algo, body, want)), f
+    b.close()
+
+
+def test_batch_other_window_dense(hg):
+    import paper_1202_3669_b300 as hgb
+    sizes = G.lognormal_sizes(40, seed=43, median=60_000, sigma=1.0, hi=1 << 20)
+    data, off = G.files_from_sizes(sizes, 44)
+    p = P(window=33, mask_bits=3, magic=2, min_chunk=100, max_chunk=1000)
+    b = hgb.Batch(hg, off, p)
+    out = b.cdc_hash(to_device(data, 1), hgb.MD5)
+    b.sync()
+    for f in range(len(sizes)):
+        body = data[off[f]:off[f + 1]]
+        want = oracle.cdc(body, 33, 3, 2, 100, 1000, nthreads=8, kind=R)
+        ends, dg = b.file_results(f, *out)
+        assert np.array_equal(ends, want), f
+        assert np.array_equal(dg, oracle.hash_chunks(oracle.MD5, body, want)), f
+    b.close()
+
+
+def test_server(hg):
+    """A server whose chunking requests use the Rabin window: exact per request."""
+    import paper_1202_3669_b300 as hgb
+    srv = hgb.Server(hg, device_budget=512 << 20, max_wave_bytes=32 << 20, max_wave_requests=16, p=P())
+    sizes = G.lognormal_sizes(30, seed=45, median=50_000, sigma=1.6, hi=4 << 20)
+    reqs = [(G.uniform_bytes(int(z), 4600 + i), hgb.HG_REQ_CDC, hgb.SHA1 if i % 2 else hgb.MD5, 0, False)
+            for i, z in enumerate(sizes)]
+    tickets = [srv.submit(*r) for r in reqs]
+    for (data, _, algo, _, _), t in zip(reqs, tickets):
+        res = srv.poll(t)
+        assert res["status"] == 0
+        want = oracle.cdc(data, 48, 13, 0x0F0F, 2048, 65536, nthreads=8, kind=R)
+        assert np.array_equal(res["ends"].astype(np.uint64), want)
+        assert np.array_equal(res["digests"], oracle.hash_chunks(algo, data, want))
+    srv.close()
