@@ -54,7 +54,9 @@ ALU_OPS_PER_WINDOW = 208
 ALU_LANES_PER_SM_CLK = 64     # integer ALU pipe: one warp instruction per 2 clocks per scheduler
 SURVEY_OPS_PER_WINDOW = 270   # the same work counted in 2-input operations
 ISSUE_LANES_PER_SM_CLK = 128  # 4 schedulers x 32 lanes
-WINDOW_KERNEL_SRC = os.path.join(ROOT, "paper_1202_3669_b300", "csrc", "hg_cdc.cu")
+# the window kernel's own sources: its counters in profiles/ hold only while these are unchanged
+WINDOW_KERNEL_SRC = [os.path.join(ROOT, "paper_1202_3669_b300", "csrc", f)
+                     for f in ("hg_window.cu", "hg_window.cuh", "hg_device.cuh")]
 
 
 def parse():
@@ -150,15 +152,23 @@ def measured_peaks():
     return {"hbm_gbs": 6400.0, "sm_max_mhz": 2032.0}, "fallback"
 
 
-def kernel_traffic(kernel: str, src: str):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on this source."""
+def source_hash(srcs) -> str:
+    """First 16 hex digits of the SHA-256 of the source files, concatenated in order."""
+    h = hashlib.sha256()
+    for src in srcs:
+        with open(src, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def kernel_traffic(kernel: str, srcs):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on these sources."""
     p = os.path.join(ROOT, "profiles", f"{kernel}.traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         rec = json.load(f)
-    with open(src, "rb") as f:
-        h = hashlib.sha256(f.read()).hexdigest()[:16]
+    h = source_hash(srcs)
     if rec.get("source_sha256_16") != h:
         return None
     return rec
