@@ -49,10 +49,11 @@ WORKLOAD = "cdc_64MiB_base_plus_1pct_edited_version"
 # Algorithmic cost of one window hash in integer-ALU instructions (3-input logic op,
 # 3-input add and the rotate-add each count one): 42 operations with a constant
 # message word x 3 + 19 with a data word x 4, + 3.75 funnel shifts to assemble
-# the window, + 4 for the test and bit collection = 208 (derivation in the design doc).
+# the window, + 4 for the test and bit collection = 208 (ncu counted 194 ALU-pipe + 10
+# FMA-pipe instructions per window).
 ALU_OPS_PER_WINDOW = 208
 ALU_LANES_PER_SM_CLK = 64     # integer ALU pipe: one warp instruction per 2 clocks per scheduler
-SURVEY_OPS_PER_WINDOW = 270   # the same work counted in 2-input operations
+TWO_INPUT_OPS_PER_WINDOW = 270  # the same work counted in 2-input operations
 ISSUE_LANES_PER_SM_CLK = 128  # 4 schedulers x 32 lanes
 # the window kernel's own sources: its counters in profiles/ hold only while these are unchanged
 WINDOW_KERNEL_SRC = [os.path.join(ROOT, "paper_1202_3669_b300", "csrc", f)
@@ -456,7 +457,7 @@ def main():
                              f"{sm_max:.0f} MHz (max SM clock, {peak_kind} clock); recipe unit counts",
                 "ops_per_window": ALU_OPS_PER_WINDOW, "windows_per_launch": windows,
                 "launch_ms": t_win * 1e3, "window_GBps": versions[0].size / t_win / 1e9,
-                "frac_survey_count_vs_issue_peak": windows * SURVEY_OPS_PER_WINDOW / t_win / 1e12 / issue_peak,
+                "frac_two_input_count_vs_issue_peak": windows * TWO_INPUT_OPS_PER_WINDOW / t_win / 1e12 / issue_peak,
                 "traffic": (tr["dram_bytes_per_launch"] * versions[0].size / tr["input_bytes"]) if tr else None}
     if clocks.get("sm_mhz"):
         roofline["frac_at_observed_clock"] = achieved / (peak_tops * clocks["sm_mhz"] / sm_max)

@@ -3,7 +3,7 @@
  *
  * A plain, slow, obviously correct C99 restatement of what the hashing hot
  * path computes, used by the test-suite, the smoke check and the CPU baseline
- * of the benchmark to judge the CUDA library. It shares no code, header,
+ * of the benchmark to check the CUDA library. It shares no code, header,
  * table or constant generator with the CUDA path, and the product never
  * links, loads or calls it.
  *
