@@ -42,10 +42,13 @@ __device__ __forceinline__ uint32_t roll(uint32_t s, uint32_t top, uint32_t out,
     return s ^ T[top << 5] ^ U[out << 5];
 }
 
-// Fills the CTA's tables for a window of wlen bytes (all kThreads threads).
+// Fills the CTA's tables for a window of wlen bytes: threads 0..255 build one
+// entry each (tabs holds 2 x 256 x 32 words); every thread of the CTA must
+// call it (it synchronises the CTA).
+static_assert(kThreads >= 256 && kThreads % 32 == 0, "one table entry per thread of the first 256");
 __device__ __forceinline__ void build_tables(uint32_t *tabs, uint32_t wlen) {
     const int t = threadIdx.x, lane = t & 31;
-    {
+    if (t < 256) {
         // T[v] = v x^31 mod P, bit 31 = v's bit 0; thread t builds entry t and
         // writes its 32 replicas in rotated order (one bank per lane per store)
         uint32_t r = (uint32_t)t;
@@ -57,7 +60,7 @@ __device__ __forceinline__ void build_tables(uint32_t *tabs, uint32_t wlen) {
         for (int l = 0; l < 32; l++) tabs[t * 32 + ((l + lane) & 31)] = r;
     }
     __syncthreads();
-    {
+    if (t < 256) {
         // U[b] = b x^(8W) mod P: W byte steps from b, with T
         uint32_t r = (uint32_t)t;
         for (uint32_t i = 0; i < wlen; i++) r = (r << 8) ^ tabs[(r >> 23) * 32 + lane];
