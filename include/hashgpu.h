@@ -309,7 +309,9 @@ int hg_batch_autotune(hg_batch *batch, int algo, const uint8_t *d_data, uint64_t
  * computation). One progress thread per server admits requests in arrival
  * order while their input fits in a device arena of device_budget bytes
  * (allocated once at creation, with the per-wave scratch carved from the same
- * budget), copies them to the device on a copy stream, and runs everything
+ * budget), copies them to the device on a copy stream (inputs up to 512 KiB
+ * that lie in pinned host memory the device has mapped are pulled by one
+ * gather kernel per wave instead of one copy call each), and runs everything
  * admitted together as one wave: one batched chunking job for the chunking
  * requests and the fixed-block kernels for the block requests, then one copy
  * of the wave's outputs to pinned host memory. Up to max_inflight_waves waves
@@ -346,7 +348,7 @@ typedef struct {
     uint64_t device_budget;       /* device bytes for staging + wave scratch (32 GiB) */
     uint64_t max_wave_bytes;      /* input bytes per wave; larger requests are refused (1 GiB) */
     uint32_t max_wave_requests;   /* requests per wave (4096) */
-    uint32_t max_inflight_waves;  /* waves on the GPU at once, 1..8 (2) */
+    uint32_t max_inflight_waves;  /* waves on the GPU at once, 1..8 (3) */
     hg_cdc_params cdc;            /* chunking parameters of HG_REQ_CDC requests */
 } hg_server_config;
 

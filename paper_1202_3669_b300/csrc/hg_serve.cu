@@ -7,8 +7,13 @@
 //   admission  -- outstanding requests are admitted in arrival order while
 //                 their input fits in the device arena (one allocation made
 //                 at start, the device budget) and the wave limits allow;
-//   staging    -- each admitted input is copied host -> device on a copy
-//                 stream; the wave's compute waits on that copy in-stream;
+//   staging    -- admitted inputs go host -> device on a copy stream: inputs
+//                 in mapped pinned memory up to kGatherMax bytes are pulled by
+//                 one gather kernel per wave (a copy call costs ~6 us whatever
+//                 its size, so the log-normal mix of small requests ran at
+//                 42.5 GB/s as one copy each against 55 GB/s for large
+//                 copies), larger or unmapped ones by one copy call each;
+//                 the wave's compute waits on the staging in-stream;
 //   waves      -- all requests admitted together run as one wave: one batched
 //                 chunking job (hg_job.cu) for the chunking requests plus the
 //                 fixed-block kernels for the block requests, then one copy
@@ -89,12 +94,59 @@ class RangeAlloc {
 
 enum State { kQueued, kAdmitted, kDone };
 
+// Inputs up to this size in mapped pinned host memory are gathered by kernel.
+constexpr uint64_t kGatherMax = 512 << 10;
+
+// One input to gather: n bytes from host memory (device-visible address src)
+// to the arena (dst, 256-byte aligned, room for n rounded up to 256 bytes).
+struct GatherEnt {
+    const uint8_t *src;
+    uint8_t *dst;
+    uint64_t n;
+};
+
+// One CTA per input. Each warp covers 32 destination words (128 bytes) per
+// step: lanes load 32 consecutive aligned source words (one coalesced read)
+// plus the word after them (lane 31), and shift the pair into place, so the
+// source may start at any byte. Only aligned words holding request bytes are
+// read; the last destination word may carry bytes past n (the arena range is
+// rounded up to 256 bytes). Four steps are loaded before they are stored.
+__global__ void __launch_bounds__(256) k_gather(const GatherEnt *__restrict__ ents) {
+    const GatherEnt e = ents[blockIdx.x];
+    const uintptr_t s0 = reinterpret_cast<uintptr_t>(e.src);
+    const uint32_t r8 = (uint32_t)(s0 & 3) * 8;
+    const uint32_t *sw = reinterpret_cast<const uint32_t *>(s0 & ~(uintptr_t)3);
+    const uint64_t nsw = (s0 + e.n + 3) / 4 - s0 / 4;        // aligned source words with request bytes
+    const uint64_t ndw = (e.n + 3) / 4;                       // destination words
+    uint32_t *dw = reinterpret_cast<uint32_t *>(e.dst);
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    constexpr int U = 4;
+    for (uint64_t base = (uint64_t)warp * 32 * U; base < ndw; base += (uint64_t)nwarps * 32 * U) {
+        uint32_t v[U], x[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const uint64_t k = base + (uint64_t)u * 32 + lane;
+            v[u] = k < nsw ? sw[k] : 0u;
+            const uint64_t k2 = base + (uint64_t)u * 32 + 32;
+            x[u] = (lane == 31 && k2 < nsw) ? sw[k2] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            uint32_t nx = __shfl_down_sync(0xffffffffu, v[u], 1);
+            if (lane == 31) nx = x[u];
+            const uint64_t k = base + (uint64_t)u * 32 + lane;
+            if (k < ndw) dw[k] = __funnelshift_r(v[u], nx, r8);
+        }
+    }
+}
+
 struct Req {
     uint64_t ticket = 0;
     hg_request rq{};
     State state = kQueued;
     int status = HG_OK;
     uint64_t arena_off = 0, arena_bytes = 0;
+    const uint8_t *d_src = nullptr;   // device-visible address of the input (mapped pinned), or null
     uint64_t t_submit = 0, t_admit = 0, t_done = 0;
     // results (host)
     std::vector<uint64_t> ends;
@@ -131,6 +183,7 @@ struct WaveSlot {
     size_t arrays_bytes = 0, out_bytes = 0;
     char *d_arrays = nullptr, *d_out = nullptr, *h_out = nullptr;
     BlkReq *d_blkreq = nullptr, *h_blkreq = nullptr;
+    GatherEnt *h_gather = nullptr, *d_gather = nullptr;   // mapped pinned gather list
     cudaStream_t s_cdc = nullptr, s_blk = nullptr;   // this slot's compute streams
     cudaEvent_t ev_staged = nullptr, ev_blk = nullptr;
     bool busy = false;
@@ -176,7 +229,7 @@ void hg_server_default_config(hg_server_config *c) {
     c->device_budget = 32ull << 30;
     c->max_wave_bytes = 1ull << 30;
     c->max_wave_requests = 4096;
-    c->max_inflight_waves = 2;
+    c->max_inflight_waves = 3;
     hg_cdc_default_params(&c->cdc);
 }
 
@@ -223,7 +276,9 @@ int hg_server_create(hg_ctx *ctx, const hg_server_config *cfg, hg_server **out) 
     for (auto &ws : S->slots) {
         if (rc != HG_OK) break;
         if (cudaMalloc(&ws.dmem, ws.dbytes) != cudaSuccess ||
-            cudaHostAlloc(&ws.hmem, ws.hbytes, cudaHostAllocDefault) != cudaSuccess) {
+            cudaHostAlloc(&ws.hmem, ws.hbytes, cudaHostAllocDefault) != cudaSuccess ||
+            cudaHostAlloc(&ws.h_gather, R * sizeof(GatherEnt), cudaHostAllocMapped) != cudaSuccess ||
+            cudaHostGetDevicePointer((void **)&ws.d_gather, ws.h_gather, 0) != cudaSuccess) {
             cudaGetLastError();
             rc = HG_ENOMEM;
             break;
@@ -269,6 +324,7 @@ int hg_server_create(hg_ctx *ctx, const hg_server_config *cfg, hg_server **out) 
         for (auto &ws : S->slots) {
             if (ws.dmem) cudaFree(ws.dmem);
             if (ws.hmem) cudaFreeHost(ws.hmem);
+            if (ws.h_gather) cudaFreeHost(ws.h_gather);
             if (ws.s_cdc) cudaStreamDestroy(ws.s_cdc);
             if (ws.s_blk) cudaStreamDestroy(ws.s_blk);
             if (ws.ev_staged) cudaEventDestroy(ws.ev_staged);
@@ -301,6 +357,7 @@ int hg_server_destroy(hg_server *S) {
     for (auto &ws : S->slots) {
         if (ws.dmem) cudaFree(ws.dmem);
         if (ws.hmem) cudaFreeHost(ws.hmem);
+        if (ws.h_gather) cudaFreeHost(ws.h_gather);
         if (ws.s_cdc) cudaStreamDestroy(ws.s_cdc);
         if (ws.s_blk) cudaStreamDestroy(ws.s_blk);
         if (ws.ev_staged) cudaEventDestroy(ws.ev_staged);
@@ -327,6 +384,15 @@ int hg_submit(hg_server *S, const hg_request *r, uint64_t *ticket) {
     auto q = std::make_shared<Req>();
     q->rq = *r;
     q->t_submit = now_ns();
+    if (r->n && r->n <= kGatherMax) {
+        // gather by kernel only from pinned host memory the server's device has mapped
+        cudaPointerAttributes a{};
+        if (cudaPointerGetAttributes(&a, r->h_data) == cudaSuccess && a.type == cudaMemoryTypeHost &&
+            a.devicePointer && a.device == S->ctx->device)
+            q->d_src = static_cast<const uint8_t *>(a.devicePointer);
+        else
+            cudaGetLastError();
+    }
     {
         std::lock_guard<std::mutex> g(S->mu);
         if (S->fatal) return S->fatal;
@@ -427,9 +493,17 @@ int hg_server_get_stats(hg_server *S, hg_server_stats *st) {
 static int launch_wave(hg_server *S, Wave &w) {
     WaveSlot &ws = S->slots[w.slot];
     const hg_cdc_params &p = S->cfg.cdc;
-    // inputs: copy each admitted request to its arena range on the copy stream
+    // inputs: small mapped ones gathered by one kernel, the others one copy each,
+    // all on the copy stream
+    uint32_t ng = 0;
     for (auto &q : w.reqs)
-        if (q->rq.n &&
+        if (q->rq.n && q->d_src) ws.h_gather[ng++] = GatherEnt{q->d_src, (uint8_t *)S->arena + q->arena_off, q->rq.n};
+    if (ng) {
+        k_gather<<<ng, 256, 0, S->copy_s>>>(ws.d_gather);
+        if (cudaGetLastError() != cudaSuccess) return HG_ECUDA;
+    }
+    for (auto &q : w.reqs)
+        if (q->rq.n && !q->d_src &&
             cudaMemcpyAsync(S->arena + q->arena_off, q->rq.h_data, q->rq.n, cudaMemcpyHostToDevice,
                             S->copy_s) != cudaSuccess)
             return HG_ECUDA;

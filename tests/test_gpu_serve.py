@@ -153,3 +153,39 @@ def test_replay_trace(hg):
     assert (lat > 0).all() and span >= arrivals[-1]
     assert srv.stats()["completed"] == len(rq)
     srv.close()
+
+
+def test_pinned_inputs_gathered_by_kernel(hg):
+    """Inputs in pinned host memory (slices at odd offsets of one pinned pool, as a
+    service would hold them) take the gather kernel below 512 KiB and copy calls
+    above; both land exactly."""
+    import paper_1202_3669_b300 as hgb
+    pool_np = G.uniform_bytes(24 << 20, seed=901)
+    pool = torch.from_numpy(pool_np).pin_memory()
+    g = np.random.default_rng(902)
+    sizes = [1, 2, 3, 4, 5, 63, 64, 65, 4095, 4097, 100_000, 511 << 10, 512 << 10, (512 << 10) + 1,
+             3 << 20] + g.integers(1, 600_000, 40).tolist()
+    srv = hgb.Server(hg, device_budget=1 << 30, max_wave_bytes=32 << 20, max_wave_requests=64)
+    reqs = []
+    for i, z in enumerate(sizes):
+        off = int(g.integers(0, pool_np.size - z))
+        view = pool[off:off + z]
+        kind = hgb.HG_REQ_CDC if i % 3 else hgb.HG_REQ_BLOCKS
+        reqs.append((pool_np[off:off + z], view, kind))
+    tickets = []
+    for _, view, kind in reqs:
+        if kind == hgb.HG_REQ_CDC:
+            tickets.append(srv.submit(view, kind, hgb.MD5))
+        else:
+            tickets.append(srv.submit(view, kind, hgb.SHA1, 4096, True))
+    for (data, _, kind), t in zip(reqs, tickets):
+        res = srv.poll(t)
+        assert res["status"] == 0
+        if kind == hgb.HG_REQ_CDC:
+            want = oracle.cdc(data, nthreads=8)
+            assert np.array_equal(res["ends"].astype(np.uint64), want)
+            assert np.array_equal(res["digests"], oracle.hash_chunks(oracle.MD5, data, want))
+        else:
+            dg, rt = oracle.hash_blocks(oracle.SHA1, data, 4096)
+            assert np.array_equal(res["digests"], dg) and res["root"] == rt
+    srv.close()
