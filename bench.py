@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the direct/batch/serve/CPU legs")
     ap.add_argument("--leg", default=None,
-                    choices=["direct", "batch", "serve", "rabin", "blockmap", "configs"],
+                    choices=["direct", "batch", "serve", "rabin", "blockmap", "configs", "alu"],
                     help="run only this extra leg (for profiling) and print its result")
     ap.add_argument("--batch-files", type=int, default=4096,
                     help="batch leg: use only the first N files of the 4096-file workload")
@@ -288,6 +288,8 @@ def main():
             res = blockmap_leg(hgb, ctx, dev, flush)
         elif args.leg == "configs":
             res = configs_leg(hgb, ctx, dev, flush)
+        elif args.leg == "alu":
+            res = alu_leg(hgb, ctx, dev)
         else:
             res = serve_leg(hgb, ctx, batch_leg(hgb, ctx, dev, flush)["batched_graph_GBps"])
         print(json.dumps({"leg": args.leg, "result": res}), flush=True)
@@ -461,6 +463,8 @@ def main():
                 "traffic": (tr["dram_bytes_per_launch"] * versions[0].size / tr["input_bytes"]) if tr else None}
     if clocks.get("sm_mhz"):
         roofline["frac_at_observed_clock"] = achieved / (peak_tops * clocks["sm_mhz"] / sm_max)
+    # the integer pipe's rate measured by a probe (per operation class), beside the peak used
+    roofline["measured_int_pipe"] = alu_leg(hgb, ctxs[0], dev)
 
     # shared-chunk fraction between the versions (from this run's device results)
     k0, k1 = int(cnts[0].item()), int(cnts[1].item())
@@ -555,6 +559,33 @@ def direct_leg(hgb, ctx, dev, flush):
     res["note"] = (f"1 GiB uniform bytes (seed 4); 262144 / 16384 / 1024 blocks; two-level = "
                    f"H(4 KiB segment digests) per 1 MiB block; HBM peak {peaks['hbm_gbs']} GB/s ({kind})")
     return res
+
+
+def alu_leg(hgb, ctx, dev, iters=65536):
+    """Integer-pipe throughput probe (hg_probe_int_pipe): 8 CTAs x 256 threads per SM, 8
+    independent chains per thread, per operation class; lanes per clock per SM at the
+    maximum SM clock (the clock the bench runs at, sampled alongside)."""
+    import torch
+    s = torch.cuda.current_stream(dev)
+    peaks, _ = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    out = {}
+    for kind, name in ((0, "lop3"), (1, "iadd3"), (2, "shf_funnel"), (3, "md5_op_mix")):
+        ts = []
+        for i in range(5):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            ops = ctx.probe_int_pipe(kind, iters, 8, stream=s)
+            b.record(s)
+            if i >= 2:
+                ts.append((a, b))
+        torch.cuda.synchronize()
+        t = statistics.median(x.elapsed_time(y) for x, y in ts) / 1e3
+        out[name] = {"Tops": ops / t / 1e12, "lanes_per_sm_clk": ops / t / (sms * sm_max * 1e6)}
+    ctx.sync()
+    out["note"] = f"{sms} SMs at {sm_max:.0f} MHz; md5_op_mix counts 4 ops per MD5-like step"
+    return out
 
 
 def configs_leg(hgb, ctx, dev, flush):

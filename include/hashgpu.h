@@ -386,6 +386,19 @@ int hg_server_replay(hg_server *srv, const hg_request *reqs, const uint64_t *arr
                      uint32_t nreq, uint64_t *latency_ns, uint64_t *span_ns);
 
 /*
+ * Integer-pipe throughput probe (a measurement utility; the paper has no
+ * counterpart): launches, on stream, ctas_per_sm (1..8) CTAs of 256 threads
+ * per SM, each thread running 8 independent chains of `iters` operations of
+ * one class -- kind 0: 3-input logic (lop3), 1: 3-input add, 2: funnel
+ * shift, 3: the MD5 operation mix (logic, 3-input add, rotate, add: 4 ops).
+ * *ops_out receives the number of operations the launch performs; time the
+ * launch on the stream and divide by time x SMs x clock for lanes per clock
+ * per SM, the peak of the integer rooflines.
+ */
+int hg_probe_int_pipe(hg_ctx *ctx, int kind, uint32_t iters, uint32_t ctas_per_sm,
+                      uint64_t *ops_out, void *stream);
+
+/*
  * Device block map: similarity detection by digests (Sec. 2.1: identical
  * blocks have equal identifiers; Sec. 4.3: the share of a new version found in
  * chunks already stored). A hash table of distinct digests (algo fixes the

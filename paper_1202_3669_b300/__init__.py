@@ -24,7 +24,7 @@ from ._lib import (HG_MD5, HG_SHA1, HashGPUError, check, default_params,  # noqa
                    hg_submit, hg_cdc_hash, hg_cdc_hash_plan, hg_cdc_hash_h2d, hg_stream_open,
                    hg_stream_feed, hg_stream_close, hg_stream_destroy, hg_blockmap_create,
                    hg_blockmap_insert, hg_blockmap_lookup, hg_blockmap_count, hg_blockmap_clear,
-                   hg_blockmap_destroy)
+                   hg_blockmap_destroy, hg_probe_int_pipe)
 
 MD5, SHA1 = HG_MD5, HG_SHA1
 DIGEST_LEN = {MD5: 16, SHA1: 20}
@@ -100,6 +100,10 @@ class Context:
         check(hg_hash_blocks(self.h, algo, _ptr(data), n, block, _ptr(out),
                              _ptr(root_out) if root else None, _stream(stream)), "hg_hash_blocks")
         return out, (root_out if root else None)
+
+    def probe_int_pipe(self, kind: int, iters: int, ctas_per_sm: int = 8, stream=None) -> int:
+        """Launch the integer-pipe probe; returns the operations it performs (time it)."""
+        return hg_probe_int_pipe(self.h, kind, iters, ctas_per_sm, _stream(stream))
 
     def hash_blocks_pmd(self, data: torch.Tensor, block: int, segment: int, algo: int = MD5,
                         out: torch.Tensor | None = None, seg_out: torch.Tensor | None = None,

@@ -69,6 +69,7 @@ SIGNATURES = {
     "hg_scratch_bytes": (_u64, [_vp]),
     "hg_hash_blocks": (_i32, [_vp, _i32, _vp, _u64, _u64, _vp, _vp, _vp]),
     "hg_hash_blocks_pmd": (_i32, [_vp, _i32, _vp, _u64, _u64, _u64, _vp, _vp, _vp]),
+    "hg_probe_int_pipe": (_i32, [_vp, _i32, _u32, _u32, _vp, _vp]),
     "hg_blockmap_create": (_i32, [_vp, _i32, _u64, _vp]),
     "hg_blockmap_insert": (_i32, [_vp, _vp, _u64, _vp, _vp]),
     "hg_blockmap_lookup": (_i32, [_vp, _vp, _vp, _u64, _vp, _vp, _vp, _vp]),
@@ -299,6 +300,12 @@ def hg_cdc_hash_plan(n, bounds_ptr, max_n) -> int:
 def hg_cdc_hash_h2d(ctx, algo, h_in, d_in, n, params, d_ends, cap, d_count, d_digests, stream) -> int:
     return lib.hg_cdc_hash_h2d(ctx, algo, h_in, d_in, n, C.byref(params), d_ends, cap, d_count,
                                d_digests, stream)
+
+
+def hg_probe_int_pipe(ctx, kind, iters, ctas_per_sm, stream) -> int:
+    ops = C.c_uint64()
+    check(lib.hg_probe_int_pipe(ctx, kind, iters, ctas_per_sm, C.byref(ops), stream), "hg_probe_int_pipe")
+    return ops.value
 
 
 def hg_blockmap_create(ctx, algo, capacity) -> int:

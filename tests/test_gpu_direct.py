@@ -143,3 +143,15 @@ def test_two_level_bad_arguments(hg):
     with pytest.raises(hgb.HashGPUError):
         hg.hash_blocks_pmd(d, 4096, 1024, hgb.MD5, seg_out=seg[4:])   # misaligned segment digests
     hg.sync()
+
+
+def test_int_pipe_probe_runs(hg):
+    """The integer-pipe probe (roofline denominator) launches and reports its op count."""
+    import paper_1202_3669_b300 as hgb
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    for kind in range(4):
+        ops = hg.probe_int_pipe(kind, 64, 2)
+        assert ops == sms * 2 * 256 * 8 * 64 * (4 if kind == 3 else 1)
+    with pytest.raises(hgb.HashGPUError):
+        hg.probe_int_pipe(4, 64, 2)
+    hg.sync()
