@@ -81,8 +81,8 @@ typedef enum { HG_WIN_MD5 = 0, HG_WIN_RABIN = 1 } hg_window_hash;
  * the first candidate c with s + min_chunk <= c <= s + max_chunk; with none,
  * s + max_chunk if that is < n, else n.
  * Supported: 1 <= window <= 55 (MD5) or 64 (Rabin), 1 <= mask_bits <= 32,
- * magic < 2^mask_bits, 1 <= min_chunk <= max_chunk. The batch and server
- * calls support HG_WIN_MD5 only (HG_EUNSUPPORTED otherwise).
+ * magic < 2^mask_bits, 1 <= min_chunk <= max_chunk. Every chunking call,
+ * the batch and server calls included, accepts both window hashes.
  */
 typedef struct {
     uint32_t window;      /* bytes per window (20) */
@@ -116,6 +116,48 @@ int hg_reserve(hg_ctx *ctx, uint64_t max_bytes);
 int hg_sync(hg_ctx *ctx, void *stream);
 /* Bytes of scratch currently held by the context. */
 uint64_t hg_scratch_bytes(const hg_ctx *ctx);
+
+/*
+ * Pinned host buffers from a pool owned by the context: the library allocator
+ * the paper asks for. Data the application writes into page-locked host
+ * memory crosses the host link in one DMA copy (Sec. 3.1, "One-copy host to
+ * device data transfers"), and page-locked buffers are too costly to allocate
+ * per request, so they are allocated once and reused (Sec. 3.1, "Hiding memory
+ * allocation overheads"; Sec. 3.2.3, the runtime's memory-management module;
+ * Sec. 3.2.4, buffers obtained through the library call).
+ *
+ * hg_alloc_pinned: a page-locked host buffer of at least `bytes` bytes,
+ *   mapped for device access (usable as h_in of hg_cdc_hash_h2d and as
+ *   hg_request.h_data, whose small inputs the server then gathers with one
+ *   kernel). Sizes are rounded up to a class (64 KiB, else the next of
+ *   2^k x {1, 1.25, 1.5, 1.75}, hg_pinned_class); a free buffer of the class
+ *   (or a larger one up to twice it) is reused without a new host allocation.
+ *   A new allocation counts against the pool's host budget (16 GiB unless set),
+ *   releasing free buffers, largest first, if needed. Returns NULL when ctx is
+ *   NULL, bytes is 0, the budget cannot hold the buffer, or the host
+ *   allocation fails. Thread-safe.
+ * hg_free_pinned: gives p back to the pool (it stays allocated, for reuse).
+ *   p must come from hg_alloc_pinned on the same context and no enqueued work
+ *   may still read or write it (synchronise first). HG_EINVAL for a pointer
+ *   the pool does not own or that is already free.
+ * hg_pinned_set_budget: host bytes the pool may hold (0 = 16 GiB); free
+ *   buffers above a lowered budget are released at once, busy ones as they
+ *   are freed.
+ * hg_pinned_trim: releases every free buffer.
+ * hg_pinned_stats: bytes held / handed out, host allocations made, requests
+ *   served by reuse, and buffers owned.
+ * All buffers, free or not, are released by hg_destroy.
+ */
+typedef struct {
+    uint64_t budget_bytes, held_bytes, in_use_bytes;
+    uint64_t host_allocs, reuses, buffers;
+} hg_pinned_info;
+void *hg_alloc_pinned(hg_ctx *ctx, size_t bytes);
+int hg_free_pinned(hg_ctx *ctx, void *p);
+int hg_pinned_set_budget(hg_ctx *ctx, uint64_t bytes);
+int hg_pinned_trim(hg_ctx *ctx);
+int hg_pinned_stats(hg_ctx *ctx, hg_pinned_info *out);
+uint64_t hg_pinned_class(uint64_t bytes);
 
 /*
  * Direct hashing, Sec. 2.1 "Direct Hashing" and Sec. 3.2.2: the digest of
@@ -194,11 +236,13 @@ int hg_hash_chunks(hg_ctx *ctx, int algo, const uint8_t *d_in, uint64_t n, const
  * results as hg_cdc_boundaries followed by hg_hash_chunks (Fig. 3: sliding-
  * window hashing, boundary detection, then direct hashing of each chunk). The
  * launches are captured once into a CUDA graph (per context, replayed while
- * the arguments stay the same). Buffers above 64 MiB are processed in
- * segments of at least 32 MiB: every chunk is digested as soon as the
- * candidates seen so far decide its end, while later segments are still being
- * window-hashed. Runs on context-owned streams forked from and joined back
- * into `stream`. d_ends needs cap >= n / min_chunk + 1 entries (HG_ECAPACITY
+ * the arguments stay the same). Buffers above 64 MiB are window-hashed and
+ * their boundaries selected in segments of at least 32 MiB (hg_cdc_hash_plan
+ * gives the bounds), each segment's selection overlapping the next segment's
+ * window hashing; the chunk digests of such buffers run in one launch after
+ * the last selection, longest chunks first. Up to 64 MiB the buffer is one
+ * segment and its digests follow its selection. Runs on context-owned
+ * streams forked from and joined back into `stream`. d_ends needs cap >= n / min_chunk + 1 entries (HG_ECAPACITY
  * otherwise, before anything is enqueued); d_digests cap * dlen bytes;
  * *d_count (device) gets the count.
  */
@@ -438,18 +482,20 @@ int hg_blockmap_destroy(hg_blockmap *map);
  * for callers that cannot call cudaMalloc -- a write path that must not stall
  * on the device-wide synchronisation cudaMalloc/cudaFree can cause, a process
  * whose device memory belongs to another allocator, or a service whose device
- * footprint must be fixed at load time. (The paper has no counterpart: its
- * runtime preallocates buffers per job instead, Sec. 3.2.3.)
+ * footprint must be fixed at load time. The paper has no counterpart.
  * No context is needed and nothing is allocated or freed: the scratch lives in
  * one static device array of the library (about 3.1 MiB, held by every GPU
  * that loads the library until the process exits). Inputs above
  * HG_STATIC_MAX_BYTES are rejected with HG_ECAPACITY before anything is
  * enqueued. Runs on the current CUDA device. Its first call on each device
- * looks up that device's address of the array; make that first call before
- * any stream capture. All calls share the one array: calls whose work
- * overlaps on the GPU (two streams, two host threads) race and corrupt each
- * other's results, so serialise them. If a bounded device-side wait gave up,
- * *d_count is set to UINT64_MAX. Other arguments and results as for
+ * looks up that device's address of the array and does the per-device
+ * set-up of both window hashes (MD5 and Rabin); make that first call before
+ * any stream capture. The looked-up address is kept for the life of the
+ * process: after cudaDeviceReset on a device it is stale, so do not use this
+ * call on a device that was reset. All calls share the one array: calls whose
+ * work overlaps on the GPU (two streams, two host threads) race and corrupt
+ * each other's results, so serialise them. If a bounded device-side wait gave
+ * up, *d_count is set to UINT64_MAX. Other arguments and results as for
  * hg_cdc_boundaries.
  */
 #define HG_STATIC_MAX_BYTES (16ull << 20)

@@ -24,7 +24,9 @@ from ._lib import (HG_MD5, HG_SHA1, HashGPUError, check, default_params,  # noqa
                    hg_submit, hg_cdc_hash, hg_cdc_hash_plan, hg_cdc_hash_h2d, hg_stream_open,
                    hg_stream_feed, hg_stream_close, hg_stream_destroy, hg_blockmap_create,
                    hg_blockmap_insert, hg_blockmap_lookup, hg_blockmap_count, hg_blockmap_clear,
-                   hg_blockmap_destroy, hg_probe_int_pipe)
+                   hg_blockmap_destroy, hg_probe_int_pipe, hg_alloc_pinned, hg_free_pinned,
+                   hg_pinned_set_budget, hg_pinned_trim, hg_pinned_stats, hg_pinned_class,
+                   hg_pinned_info)
 
 MD5, SHA1 = HG_MD5, HG_SHA1
 DIGEST_LEN = {MD5: 16, SHA1: 20}
@@ -60,6 +62,33 @@ def _stream(stream) -> int:
     return s.cuda_stream
 
 
+class PinnedBuffer:
+    """A page-locked host buffer from a context's pool (hg_alloc_pinned).
+
+    `tensor` is a uint8 CPU tensor of the requested length over the buffer (torch
+    sees it as pinned, so copies from it are asynchronous); it must not be used
+    after `free()`, which gives the buffer back to the pool for reuse.
+    """
+
+    def __init__(self, ctx: "Context", nbytes: int):
+        self.ctx, self.nbytes = ctx, int(nbytes)
+        self.ptr = hg_alloc_pinned(ctx.h, self.nbytes)
+        if not self.ptr:
+            raise HashGPUError(_lib.HG_ENOMEM, "hg_alloc_pinned")
+        raw = (C.c_uint8 * self.nbytes).from_address(self.ptr)
+        self.tensor = torch.from_numpy(np.ctypeslib.as_array(raw))
+        ctx._pinned.add(self)
+
+    def numpy(self) -> np.ndarray:
+        return self.tensor.numpy()
+
+    def free(self) -> None:
+        if self.ptr and self.ctx.h:
+            check(hg_free_pinned(self.ctx.h, self.ptr), "hg_free_pinned")
+        self.ctx._pinned.discard(self)
+        self.ptr, self.tensor = None, None
+
+
 class Context:
     """One library context on one CUDA device (scratch memory under a budget)."""
 
@@ -68,11 +97,31 @@ class Context:
             raise RuntimeError("HashGPU needs a CUDA device")
         self.device = torch.device("cuda", device)
         self.h = hg_init(device, budget)
+        self._pinned = set()
 
     def close(self):
         if getattr(self, "h", None):
+            for b in list(getattr(self, "_pinned", ())):   # hg_destroy releases the pool
+                b.ptr, b.tensor = None, None
+            self._pinned = set()
             hg_destroy(self.h)
             self.h = None
+
+    # ---------------------------------------------------------------------------------------
+    def alloc_pinned(self, nbytes: int) -> PinnedBuffer:
+        """A pinned host buffer of nbytes from this context's pool."""
+        return PinnedBuffer(self, nbytes)
+
+    def pinned_stats(self) -> dict:
+        info = hg_pinned_info()
+        check(hg_pinned_stats(self.h, info), "hg_pinned_stats")
+        return {k: int(getattr(info, k)) for k, _ in info._fields_}
+
+    def set_pinned_budget(self, nbytes: int) -> None:
+        check(hg_pinned_set_budget(self.h, nbytes), "hg_pinned_set_budget")
+
+    def trim_pinned(self) -> None:
+        check(hg_pinned_trim(self.h), "hg_pinned_trim")
 
     def __del__(self):
         try:

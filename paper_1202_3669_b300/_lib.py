@@ -53,6 +53,11 @@ class hg_server_config(C.Structure):
                 ("cdc", hg_cdc_params)]
 
 
+class hg_pinned_info(C.Structure):
+    _fields_ = [(k, C.c_uint64) for k in ("budget_bytes", "held_bytes", "in_use_bytes",
+                                          "host_allocs", "reuses", "buffers")]
+
+
 class hg_server_stats(C.Structure):
     _fields_ = [(k, C.c_uint64) for k in ("submitted", "completed", "cancelled", "waves",
                                           "bytes_done", "arena_used", "arena_bytes", "queued")]
@@ -107,6 +112,12 @@ SIGNATURES = {
     "hg_server_get_stats": (_i32, [_vp, C.POINTER(hg_server_stats)]),
     "hg_server_replay": (_i32, [_vp, _vp, _vp, _u32, _vp, C.POINTER(C.c_uint64)]),
     "hg_cdc_boundaries_static": (_i32, [_vp, _u64, C.POINTER(hg_cdc_params), _vp, _u64, _vp, _vp]),
+    "hg_alloc_pinned": (_vp, [_vp, _sz]),
+    "hg_free_pinned": (_i32, [_vp, _vp]),
+    "hg_pinned_set_budget": (_i32, [_vp, _u64]),
+    "hg_pinned_trim": (_i32, [_vp]),
+    "hg_pinned_stats": (_i32, [_vp, C.POINTER(hg_pinned_info)]),
+    "hg_pinned_class": (_u64, [_u64]),
 }
 
 
@@ -194,6 +205,30 @@ def hg_cdc_boundaries(ctx, d_in, n, params, d_ends, cap, d_count, stream) -> int
 
 def hg_hash_chunks(ctx, algo, d_in, n, d_ends, nchunk, d_count, d_digests, stream) -> int:
     return lib.hg_hash_chunks(ctx, algo, d_in, n, d_ends, nchunk, d_count, d_digests, stream)
+
+
+def hg_alloc_pinned(ctx, nbytes) -> int | None:
+    return lib.hg_alloc_pinned(ctx, nbytes)
+
+
+def hg_free_pinned(ctx, p) -> int:
+    return lib.hg_free_pinned(ctx, p)
+
+
+def hg_pinned_set_budget(ctx, nbytes) -> int:
+    return lib.hg_pinned_set_budget(ctx, nbytes)
+
+
+def hg_pinned_trim(ctx) -> int:
+    return lib.hg_pinned_trim(ctx)
+
+
+def hg_pinned_stats(ctx, out) -> int:
+    return lib.hg_pinned_stats(ctx, C.byref(out))
+
+
+def hg_pinned_class(nbytes) -> int:
+    return lib.hg_pinned_class(nbytes)
 
 
 def hg_cdc_boundaries_static(d_in, n, params, d_ends, cap, d_count, stream) -> int:

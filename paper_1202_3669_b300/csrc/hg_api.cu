@@ -144,6 +144,7 @@ int hg_destroy(hg_ctx *c) {
     cudaFree(c->d_segdig);
     cudaFree(c->d_tasks);
     cudaFree(c->d_err);
+    pinned_destroy(c);
     if (c->pipe_ready) {
         if (c->p_exec) cudaGraphExecDestroy(c->p_exec);
         cudaStreamDestroy(c->p_cap);

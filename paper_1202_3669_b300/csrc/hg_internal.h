@@ -2,10 +2,15 @@
 #pragma once
 #include <cstddef>
 #include <cstdint>
+#include <mutex>
 #include <vector>
 #include <cuda_runtime.h>
 
 #include "hashgpu.h"
+
+namespace hg {
+struct PinnedPool;
+}
 
 struct hg_ctx {
     int device = 0;
@@ -33,6 +38,9 @@ struct hg_ctx {
     cudaGraphExec_t p_exec = nullptr;       // replayed while p_key matches
     uint64_t p_key[16] = {};
     uint64_t scratch_gen = 0;               // bumped whenever scratch is reallocated
+    // pinned host buffer pool (hg_pinned.cu), created on first use
+    std::mutex pinned_mu;
+    struct hg::PinnedPool *pinned = nullptr;
 };
 
 namespace hg {
@@ -51,7 +59,7 @@ inline unsigned chain_grid(uint64_t ntask, unsigned lanes, unsigned threads) {
 // Candidate-list capacity used by hg_cdc_boundaries for an n-byte input. The
 // expected density is 2^-mask_bits per byte; denser inputs fall back to
 // scanning the bitmap during selection.
-inline uint64_t cand_capacity(uint64_t n) { return n / 128 + 4096; }
+constexpr uint64_t cand_capacity(uint64_t n) { return n / 128 + 4096; }
 
 // Scratch management (hg_api.cu). Grows *p to hold `count` elements of
 // `elem` bytes; returns HG_OK / HG_ENOMEM / HG_ECUDA.
@@ -159,6 +167,11 @@ int launch_select(const uint64_t *d_cands, const uint64_t *d_ncand, uint64_t can
                   uint64_t cap, uint64_t *d_count, cudaStream_t s);
 
 inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? HG_OK : HG_ECUDA; }
+
+// hg_pinned.cu: the pinned host buffer pool.
+constexpr uint64_t kPinnedDefaultBudget = 16ull << 30;
+uint64_t pinned_class(uint64_t n);
+void pinned_destroy(hg_ctx *c);   // frees every buffer of the pool (device synchronised first)
 
 // ---- batched chunking jobs (hg_job.cu) -------------------------------------------------
 // Files from this size up select their boundaries with a whole CTA.

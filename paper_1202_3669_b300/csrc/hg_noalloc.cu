@@ -23,7 +23,7 @@ namespace {
 constexpr uint64_t kMaxBytes = HG_STATIC_MAX_BYTES;
 constexpr uint64_t kMaxWords = kMaxBytes / 32;                 // bitmap words
 constexpr uint64_t kMaxTiles = kMaxBytes / kWinTile;           // window tiles
-constexpr uint64_t kMaxCands = kMaxBytes / 128 + 4096;         // = cand_capacity(kMaxBytes)
+constexpr uint64_t kMaxCands = cand_capacity(kMaxBytes);        // as hg_cdc_boundaries sizes it
 static_assert(kMaxBytes % kWinTile == 0, "maximum must be a whole number of tiles");
 
 // byte offsets of the pieces inside the array (each 256-byte aligned)
@@ -38,7 +38,10 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 // Device address of g_scratch per device. In host code `g_scratch` names a
 // host-side shadow, not device memory, so kernels get the address obtained
-// from cudaGetSymbolAddress on that device.
+// from cudaGetSymbolAddress on that device. The first call on a device also
+// does every other per-device set-up the launched kernels need (the Rabin
+// window kernels' shared-memory opt-in), so that one call made before any
+// stream capture covers both window hashes.
 constexpr int kMaxDevices = 64;
 unsigned char *g_addr[kMaxDevices] = {};
 std::mutex g_mu;
@@ -47,6 +50,8 @@ int scratch_address(int dev, unsigned char **out) {
     if (dev < 0 || dev >= kMaxDevices) return HG_EUNSUPPORTED;
     std::lock_guard<std::mutex> lock(g_mu);
     if (!g_addr[dev]) {
+        int r = rabin_prepare();
+        if (r) return r;
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) {
             cudaGetLastError();

@@ -8,6 +8,9 @@
 // are those of the MD5 window. The kernel is persistent (CTAs per SM as the
 // tables and registers allow, groups of 4 tiles pulled in a grid-stride loop)
 // so each CTA builds its tables once.
+#include <atomic>
+#include <mutex>
+
 #include "hg_rabin.cuh"
 
 namespace hg {
@@ -60,10 +63,11 @@ __global__ void __launch_bounds__(kThreads, ctas_per_sm<GENERAL>())
 // Per device: the kernels' shared-memory opt-in (64 KiB of tables) and the SM
 // count, set up outside any stream capture (hg_init calls rabin_prepare).
 struct RabinDev {
-    bool ready = false;
+    std::atomic<bool> ready{false};   // set (release) after sms, read (acquire) before launches
     int sms = 0;
 };
 RabinDev g_rdev[64];
+std::mutex g_rmu;                     // serialises the set-up of rabin_prepare
 
 template <int W>
 cudaError_t opt_in() {
@@ -82,7 +86,7 @@ int launch_rabin_t(const uint8_t *d_in, uint64_t n, uint32_t w, uint32_t mask, u
     if (cudaGetDevice(&dev) != cudaSuccess) return HG_ECUDA;
     if (dev < 0 || dev >= 64) return HG_EUNSUPPORTED;
     int r;
-    if (!g_rdev[dev].ready && (r = rabin_prepare())) return r;
+    if (!g_rdev[dev].ready.load(std::memory_order_acquire) && (r = rabin_prepare())) return r;
     const bool general = (reinterpret_cast<uintptr_t>(d_in) & 15) != 0;
     const uint64_t ngroups = (ntiles + kTilesPerGroup - 1) / kTilesPerGroup;
     const uint64_t slots = (uint64_t)g_rdev[dev].sms * (general ? ctas_per_sm<true>() : ctas_per_sm<false>());
@@ -102,7 +106,9 @@ int rabin_prepare() {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return HG_ECUDA;
     if (dev < 0 || dev >= 64) return HG_EUNSUPPORTED;
-    if (g_rdev[dev].ready) return HG_OK;
+    if (g_rdev[dev].ready.load(std::memory_order_acquire)) return HG_OK;
+    std::lock_guard<std::mutex> lock(g_rmu);
+    if (g_rdev[dev].ready.load(std::memory_order_acquire)) return HG_OK;
     int sms = 0;
     if (opt_in<0>() || opt_in<16>() || opt_in<20>() || opt_in<24>() || opt_in<32>() ||
         opt_in<48>() || opt_in<64>() || job_rabin_prepare() != HG_OK ||
@@ -111,7 +117,7 @@ int rabin_prepare() {
         return HG_ECUDA;
     }
     g_rdev[dev].sms = sms;
-    g_rdev[dev].ready = true;
+    g_rdev[dev].ready.store(true, std::memory_order_release);
     return HG_OK;
 }
 

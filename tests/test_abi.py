@@ -72,3 +72,21 @@ def test_cdc_hash_plan_is_host_only():
             assert b == [0, n]                          # small buffers: one pass
         else:
             assert all(y - x >= (16 << 20) for x, y in zip(b, b[1:]))
+
+
+def test_pinned_size_classes_and_null_context():
+    """Pinned-pool size classes (host arithmetic only) and argument errors."""
+    from paper_1202_3669_b300 import _lib
+    L = _lib.lib
+    assert L.hg_pinned_class(0) == 0
+    assert L.hg_pinned_class(1) == 64 << 10
+    assert L.hg_pinned_class(64 << 10) == 64 << 10
+    assert L.hg_pinned_class((64 << 10) + 1) == 80 << 10
+    assert L.hg_pinned_class(1 << 20) == 1 << 20
+    assert L.hg_pinned_class((1 << 20) + 1) == (1 << 20) + (1 << 18)
+    assert L.hg_pinned_class(3 << 20) == 3 << 20
+    for n in (100, 70_000, 999_999, 5 << 20, (5 << 20) + 1, 123_456_789):
+        c = L.hg_pinned_class(n)
+        assert n <= c <= max(64 << 10, n + n // 4 + 1)
+    assert L.hg_alloc_pinned(None, 100) is None
+    assert L.hg_free_pinned(None, None) == _lib.HG_EINVAL

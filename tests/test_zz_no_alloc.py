@@ -19,14 +19,26 @@ pytestmark = pytest.mark.gpu
 
 
 def test_static_entry_matches_context_entry():
+    import os
+
+    import oracle
     import paper_1202_3669_b300 as hgb
     from paper_1202_3669_b300 import _lib
     p = hgb.default_params()
     ctx = hgb.Context(0)
     s = torch.cuda.current_stream().cuda_stream
-    # two different inputs, the second smaller, so stale scratch would show
-    for n, seed in (((12 << 20) + 4321, 71), ((3 << 20) + 17, 72)):
-        data = torch.from_numpy(G.uniform_bytes(n, seed)).cuda()
+    # calls in a row on different inputs, a smaller one after a larger one so
+    # stale scratch would show; the maximum size exactly (bitmap, tile arrays
+    # and candidate list full to their last entry); and an input that starts
+    # one byte past a 16-byte boundary (the byte-load path of the window kernel)
+    cases = (((12 << 20) + 4321, 71, 0, False), ((3 << 20) + 17, 72, 0, False),
+             (16 << 20, 73, 0, True), ((5 << 20) + 3, 74, 1, True))
+    for n, seed, off, vs_oracle in cases:
+        host = G.uniform_bytes(n, seed)
+        buf = torch.zeros(n + off, dtype=torch.uint8, device="cuda")
+        buf[off:] = torch.from_numpy(host).cuda()
+        data = buf[off:]
+        assert data.data_ptr() % 16 == off
         cap = n // p.min_chunk + 2
         e_ref, c_ref = ctx.cdc_boundaries(data, p, cap=cap)
         e_st = torch.empty(cap, dtype=torch.int64, device="cuda")
@@ -38,6 +50,9 @@ def test_static_entry_matches_context_entry():
         k = int(c_ref.item())
         assert int(c_st.item()) == k > 100
         assert torch.equal(e_st[:k], e_ref[:k])
+        if vs_oracle:
+            want = oracle.cdc(host, nthreads=os.cpu_count() or 1)
+            assert np.array_equal(e_st[:k].cpu().numpy().astype(np.uint64), want)
     ctx.sync()
     ctx.close()
 
