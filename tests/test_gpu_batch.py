@@ -10,7 +10,7 @@ import torch
 
 import oracle
 from gen import inputs as G
-from tests.gpu_util import to_device
+from tests.gpu_util import oracle_files, to_device
 
 pytestmark = pytest.mark.gpu
 
@@ -23,7 +23,7 @@ def hg():
     ctx.close()
 
 
-def check_batch(hg, sizes, seed, algo, p=None, graph=False, offset=0, sample=None):
+def check_batch(hg, sizes, seed, algo, p=None, graph=False, offset=0):
     import paper_1202_3669_b300 as hgb
     p = p or hgb.default_params()
     sizes = np.asarray(sizes, dtype=np.int64)
@@ -32,15 +32,16 @@ def check_batch(hg, sizes, seed, algo, p=None, graph=False, offset=0, sample=Non
     d = to_device(data, offset)
     out = b.cdc_hash(d, algo, graph=graph)
     b.sync()
-    files = range(len(sizes)) if sample is None else sample
-    for f in files:
-        body = data[off[f]:off[f + 1]]
-        cands = oracle.window_candidates(body, p.window, p.mask_bits, p.magic, nthreads=8)
-        want = oracle.select(cands, body.size, p.min_chunk, p.max_chunk)
-        ends, dg = b.file_results(f, *out)
-        assert np.array_equal(ends, want), (f, sizes[f], ends[:5], want[:5])
-        assert np.array_equal(dg, oracle.hash_chunks(algo, body, want)), f
+    ends_h, cnt_h, dg_h = (t.cpu().numpy() for t in out)
+    so = np.asarray(b.slot_off, dtype=np.int64)
+    got = [(ends_h[so[f]:so[f] + cnt_h[f]].astype(np.uint64), dg_h[so[f]:so[f] + cnt_h[f]])
+           for f in range(len(sizes))]
     b.close()
+    want = oracle_files(data, off, p, algo)
+    for f in range(len(sizes)):
+        (ends, dg), (we, wd) = got[f], want[f]
+        assert np.array_equal(ends, we), (f, sizes[f], ends[:5], we[:5])
+        assert np.array_equal(dg, wd), f
     return out
 
 
@@ -111,16 +112,11 @@ def test_batch_autotune_keeps_results(hg):
 
 
 def test_config_batch_4096_files(hg):
-    """4096 log-normal files (median 64 KiB, sigma 2.4, 512 B..256 MiB, ~3.6 GiB):
-    every file's chunk count is checked by the rule's own bounds and a sample of
-    files (all sizes up to 4 MiB, plus the largest below 64 MiB) against the oracle."""
-    import paper_1202_3669_b300 as hgb
+    """4096 log-normal files (median 64 KiB, sigma 2.4, 512 B..256 MiB, about 3.9 GB) in
+    one graph-replayed batch: every file's chunk ends and SHA-1 digests equal the
+    oracle's for that file alone."""
     seed, sizes = G.batch_workload_seed()
-    g = G.rng(99)
-    small = np.flatnonzero(sizes <= (4 << 20))
-    sample = sorted(set(g.choice(small, 40, replace=False).tolist()) |
-                    {int(np.flatnonzero(sizes == sizes[sizes < (64 << 20)].max())[0])})
-    out = check_batch(hg, sizes, seed=seed + 1000, algo=oracle.SHA1, graph=True, sample=sample)
+    out = check_batch(hg, sizes, seed=seed + 1000, algo=oracle.SHA1, graph=True)
     counts = out[1].cpu().numpy()
     assert (counts >= np.ceil(sizes / 65536)).all()
     assert (counts <= sizes // 2048 + 1).all()
