@@ -8,6 +8,7 @@
 // them itself.
 #pragma once
 #include <cstdint>
+#include <utility>
 
 namespace hg {
 
@@ -114,6 +115,8 @@ struct Md5 {
     __device__ __forceinline__ void init() {
         h[0] = kMd5A; h[1] = kMd5B; h[2] = kMd5C; h[3] = kMd5D;
     }
+    // Only the pipe-split forms (Md5Split, Sha1Split) use a run-time 1.
+    __device__ __forceinline__ void set_one(uint32_t) {}
     // M: little-endian message words.
     __device__ __forceinline__ void compress(const uint32_t (&M)[16]) {
         uint32_t a = h[0], b = h[1], c = h[2], d = h[3];
@@ -223,6 +226,129 @@ struct Md5Chain : Md5 {
     }
 };
 
+// ------------------------------------------------ adds on the FMA pipe -----
+// On sm_103a the logic op, the funnel shift and the rotate-add (b + rotl(x, s)
+// is one instruction) of an MD5 or SHA-1 step issue only to the integer ALU
+// pipe, which accepts one warp instruction every other cycle per scheduler;
+// the FMA pipe beside it also runs integer multiply-adds and otherwise idles
+// in these kernels. An add written as a multiply-add by a run-time 1 (`one`,
+// a kernel argument, so the compiler cannot fold the multiply away) runs on
+// the FMA pipe. Each step follows a policy:
+//   0  its adds as plain code (the compiler places them, mostly on the ALU);
+//   1  the adds that do not wait for the step's logic op (a + M + K for MD5,
+//      e + K + W for SHA-1) as plain code, the add of the logic op's result
+//      on the FMA pipe;
+//   2  all of its adds on the FMA pipe;
+//   3  the add of two words known early (a + M for MD5, e + W for SHA-1) on
+//      the FMA pipe, the rest plain: the step's dependent chain keeps the
+//      short ALU add.
+// A pattern packs the policies of eight consecutive steps, two bits each
+// (step n uses bits 2(n mod 8) .. 2(n mod 8) + 1), repeated over the steps.
+__device__ __forceinline__ uint32_t add_fma(uint32_t x, uint32_t y, uint32_t one) {
+    uint32_t r;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(x), "r"(one), "r"(y));
+    return r;
+}
+// x + k with k a constant (it lands in the instruction's immediate field).
+__device__ __forceinline__ uint32_t add_fma_k(uint32_t x, uint32_t k, uint32_t one) {
+    uint32_t r;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(one), "r"(k), "r"(x));
+    return r;
+}
+__host__ __device__ constexpr int pol_of(uint32_t pat, int n) { return (int)((pat >> (2 * (n & 7))) & 3u); }
+constexpr uint32_t kPolAllPlain = 0x0000u, kPolAll1 = 0x5555u, kPolAll2 = 0xAAAAu;
+
+// RFC 1321 Sec. 3.4: the additive constants T[1..64], the message word each
+// step reads and the rotation amounts, indexed by step n = 0..63.
+constexpr uint32_t kMd5T[64] = {
+    0xd76aa478, 0xe8c7b756, 0x242070db, 0xc1bdceee, 0xf57c0faf, 0x4787c62a, 0xa8304613, 0xfd469501,
+    0x698098d8, 0x8b44f7af, 0xffff5bb1, 0x895cd7be, 0x6b901122, 0xfd987193, 0xa679438e, 0x49b40821,
+    0xf61e2562, 0xc040b340, 0x265e5a51, 0xe9b6c7aa, 0xd62f105d, 0x02441453, 0xd8a1e681, 0xe7d3fbc8,
+    0x21e1cde6, 0xc33707d6, 0xf4d50d87, 0x455a14ed, 0xa9e3e905, 0xfcefa3f8, 0x676f02d9, 0x8d2a4c8a,
+    0xfffa3942, 0x8771f681, 0x6d9d6122, 0xfde5380c, 0xa4beea44, 0x4bdecfa9, 0xf6bb4b60, 0xbebfbc70,
+    0x289b7ec6, 0xeaa127fa, 0xd4ef3085, 0x04881d05, 0xd9d4d039, 0xe6db99e5, 0x1fa27cf8, 0xc4ac5665,
+    0xf4292244, 0x432aff97, 0xab9423a7, 0xfc93a039, 0x655b59c3, 0x8f0ccc92, 0xffeff47d, 0x85845dd1,
+    0x6fa87e4f, 0xfe2ce6e0, 0xa3014314, 0x4e0811a1, 0xf7537e82, 0xbd3af235, 0x2ad7d2bb, 0xeb86d391,
+};
+__host__ __device__ constexpr int md5_msg(int n) {
+    return n < 16 ? n : n < 32 ? (1 + 5 * n) % 16 : n < 48 ? (5 + 3 * n) % 16 : (7 * n) % 16;
+}
+__host__ __device__ constexpr int md5_rot(int n) {
+    return (n < 16)   ? ((n & 3) == 0 ? 7 : (n & 3) == 1 ? 12 : (n & 3) == 2 ? 17 : 22)
+           : (n < 32) ? ((n & 3) == 0 ? 5 : (n & 3) == 1 ? 9 : (n & 3) == 2 ? 14 : 20)
+           : (n < 48) ? ((n & 3) == 0 ? 4 : (n & 3) == 1 ? 11 : (n & 3) == 2 ? 16 : 23)
+                      : ((n & 3) == 0 ? 6 : (n & 3) == 1 ? 10 : (n & 3) == 2 ? 15 : 21);
+}
+
+// One MD5 step a = b + rotl(a + f + m + T, S) with the adds placed by policy
+// P. A message word that is a compile-time constant (DATA false) is folded
+// with T into one immediate.
+template <int P, bool DATA, int S, uint32_t T>
+__device__ __forceinline__ void md5_pstep(uint32_t &a, uint32_t b, uint32_t f, uint32_t m,
+                                          uint32_t one) {
+    uint32_t x;
+    if constexpr (!DATA) {
+        if constexpr (P == 2) x = add_fma(f, add_fma_k(a, m + T, one), one);
+        else x = a + f + (m + T);
+    } else if constexpr (P == 2) {
+        x = add_fma(f, add_fma(m, add_fma_k(a, T, one), one), one);
+    } else if constexpr (P == 1) {
+        x = add_fma(f, a + m + T, one);
+    } else if constexpr (P == 3) {
+        x = add_fma(a, m, one) + f + T;
+    } else {
+        x = a + f + m + T;
+    }
+    a = rotl(x, S) + b;
+}
+
+// Step n on the state st = {a, b, c, d}: it writes word (-n) mod 4 and reads
+// the next three in order. Bit i of DM says message word i is data (else a
+// constant after inlining); data steps take their policy from pattern PD,
+// constant steps from pattern PC.
+template <int n, uint32_t DM, uint32_t PC, uint32_t PD>
+__device__ __forceinline__ void md5_pstep_n(uint32_t (&st)[4], const uint32_t (&M)[16],
+                                            uint32_t one) {
+    constexpr int t = (4 - (n & 3)) & 3;
+    constexpr int i = md5_msg(n);
+    constexpr bool data = ((DM >> i) & 1u) != 0;
+    constexpr int P = data ? pol_of(PD, n) : pol_of(PC, n);
+    const uint32_t b = st[(t + 1) & 3], c = st[(t + 2) & 3], d = st[(t + 3) & 3];
+    uint32_t f;
+    if constexpr (n < 16) f = HG_MD5_F(b, c, d);
+    else if constexpr (n < 32) f = HG_MD5_G(b, c, d);
+    else if constexpr (n < 48) f = HG_MD5_H(b, c, d);
+    else f = HG_MD5_I(b, c, d);
+    md5_pstep<P, data, md5_rot(n), kMd5T[n]>(st[t], b, f, M[i], one);
+}
+
+template <uint32_t DM, uint32_t PC, uint32_t PD, int... N>
+__device__ __forceinline__ void md5_psteps(uint32_t (&st)[4], const uint32_t (&M)[16], uint32_t one,
+                                           std::integer_sequence<int, N...>) {
+    (md5_pstep_n<N, DM, PC, PD>(st, M, one), ...);
+}
+
+// The first NSTEPS operations of MD5 (64, or 61 for the window test) with
+// the adds split between the pipes by the patterns above.
+template <int NSTEPS, uint32_t DM, uint32_t PC, uint32_t PD>
+__device__ __forceinline__ void md5_rounds_split(uint32_t (&st)[4], const uint32_t (&M)[16],
+                                                 uint32_t one) {
+    md5_psteps<DM, PC, PD>(st, M, one, std::make_integer_sequence<int, NSTEPS>{});
+}
+
+// MD5 with the adds of every step placed by pattern PD (all message words
+// are data). `one` must be set to a run-time 1 before compress.
+template <uint32_t PD>
+struct Md5Split : Md5 {
+    uint32_t one;
+    __device__ __forceinline__ void set_one(uint32_t v) { one = v; }
+    __device__ __forceinline__ void compress(const uint32_t (&M)[16]) {
+        uint32_t st[4] = {h[0], h[1], h[2], h[3]};
+        md5_rounds_split<64, 0xffffu, kPolAllPlain, PD>(st, M, one);
+        h[0] += st[0]; h[1] += st[1]; h[2] += st[2]; h[3] += st[3];
+    }
+};
+
 // --------------------------------------------------------------- SHA-1 -----
 
 struct Sha1 {
@@ -234,6 +360,7 @@ struct Sha1 {
         h[0] = 0x67452301u; h[1] = 0xefcdab89u; h[2] = 0x98badcfeu; h[3] = 0x10325476u;
         h[4] = 0xc3d2e1f0u;
     }
+    __device__ __forceinline__ void set_one(uint32_t) {}
     // M: little-endian message words (byte-swapped here to the big-endian
     // words FIPS 180-4 Sec. 5.2.1 parses).
     __device__ __forceinline__ void compress(const uint32_t (&M)[16]) {
@@ -265,6 +392,40 @@ struct Sha1 {
         M[14] = bswap((uint32_t)(bits >> 32)); M[15] = bswap((uint32_t)bits);
     }
     __device__ __forceinline__ uint32_t out_word(int i) const { return bswap(h[i]); }
+};
+
+// SHA-1 with the adds of round t placed by policy pol_of(PAT, t) (see the
+// pipe policies above): T = rotl(a, 5) + f + e + K + W. `one` must be set to
+// a run-time 1 before compress.
+template <uint32_t PAT>
+struct Sha1Split : Sha1 {
+    uint32_t one;
+    __device__ __forceinline__ void set_one(uint32_t v) { one = v; }
+    __device__ __forceinline__ void compress(const uint32_t (&M)[16]) {
+        uint32_t W[16];
+#pragma unroll
+        for (int i = 0; i < 16; i++) W[i] = bswap(M[i]);
+        uint32_t a = h[0], b = h[1], c = h[2], d = h[3], e = h[4];
+#pragma unroll
+        for (int t = 0; t < 80; t++) {
+            if (t >= 16)
+                W[t & 15] = rotl(W[(t - 3) & 15] ^ W[(t - 8) & 15] ^ W[(t - 14) & 15] ^ W[t & 15], 1);
+            uint32_t f, k;
+            if (t < 20)      { f = d ^ (b & (c ^ d));       k = 0x5a827999u; }
+            else if (t < 40) { f = b ^ c ^ d;               k = 0x6ed9eba1u; }
+            else if (t < 60) { f = (b & c) | (d & (b | c)); k = 0x8f1bbcdcu; }
+            else             { f = b ^ c ^ d;               k = 0xca62c1d6u; }
+            const int pol = pol_of(PAT, t);
+            uint32_t x;
+            if (pol == 2) x = add_fma(f, add_fma(W[t & 15], add_fma_k(e, k, one), one), one);
+            else if (pol == 1) x = add_fma(f, e + k + W[t & 15], one);
+            else if (pol == 3) x = add_fma(e, W[t & 15], one) + f + k;
+            else x = f + e + k + W[t & 15];
+            const uint32_t T = rotl(a, 5) + x;
+            e = d; d = c; c = rotl(b, 30); b = a; a = T;
+        }
+        h[0] += a; h[1] += b; h[2] += c; h[3] += d; h[4] += e;
+    }
 };
 
 // Very few latency-bound digest chains (large fixed blocks: 1024 chains of

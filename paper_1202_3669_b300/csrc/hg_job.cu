@@ -73,7 +73,8 @@ __global__ void __launch_bounds__(kWinThreads) k_job_window(JobDev j, uint32_t w
                                                             uint32_t magic,
                                                             uint32_t *__restrict__ bitmap,
                                                             uint32_t *__restrict__ tile_cnt,
-                                                            unsigned long long *tile_ctr, int *err) {
+                                                            unsigned long long *tile_ctr, int *err,
+                                                            uint32_t one) {
     const uint32_t wlen = W ? (uint32_t)W : wrt;
     __shared__ __align__(128) uint8_t sbuf[2][kSmemBytes];
     __shared__ __align__(8) uint64_t mbar[2];
@@ -127,7 +128,7 @@ __global__ void __launch_bounds__(kWinThreads) k_job_window(JobDev j, uint32_t w
         }
         const uint64_t p0 = r.lo + 32u * (uint64_t)t;
         const uint32_t bits =
-            clip_bits(window_bits32<W>(sbuf[b], t, wlen, mask, magic), p0, wlen, r.len);
+            clip_bits(window_bits32<W>(sbuf[b], t, wlen, mask, magic, one), p0, wlen, r.len);
         bitmap[(uint64_t)cur * kWinThreads + t] = bits;
         const uint32_t c = __reduce_add_sync(0xffffffffu, (uint32_t)__popc(bits));
         if ((t & 31) == 0) warp_cnt[t >> 5] = c;
@@ -375,7 +376,7 @@ template <int W>
 void launch_job_window_t(int grid, const JobDev &j, uint32_t w, uint32_t mask, uint32_t magic,
                          uint32_t *bm, uint32_t *tc, unsigned long long *ctr, int *err,
                          cudaStream_t s) {
-    k_job_window<W><<<grid, kWinThreads, 0, s>>>(j, w, mask, magic, bm, tc, ctr, err);
+    k_job_window<W><<<grid, kWinThreads, 0, s>>>(j, w, mask, magic, bm, tc, ctr, err, 1u);
 }
 
 template <int W>

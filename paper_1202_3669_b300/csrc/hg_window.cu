@@ -16,14 +16,16 @@ namespace {
 // [tile + 32t, tile + 32t + 32) and so exactly bitmap word tile/32 + t.
 // The tile and a 64-byte halo before it are staged in shared memory, by one
 // bulk asynchronous copy (TMA) for interior tiles of a 16-byte aligned input
-// and by guarded byte loads at the edges.
+// and by guarded byte loads at the edges. `one` is 1 (the run-time 1 of the
+// FMA-pipe adds).
 template <int W>
 __global__ void __launch_bounds__(kWinThreads) k_window_bitmap(const uint8_t *__restrict__ in,
                                                                uint64_t n, uint32_t wrt,
                                                                uint32_t mask, uint32_t magic,
                                                                uint32_t *__restrict__ bitmap,
                                                                uint32_t *__restrict__ tile_cnt,
-                                                               int *err, uint32_t tile0) {
+                                                               int *err, uint32_t tile0,
+                                                               uint32_t one) {
     const uint32_t wlen = W ? (uint32_t)W : wrt;
     __shared__ __align__(128) uint8_t sbuf[kSmemBytes];
     __shared__ __align__(8) uint64_t mbar;
@@ -56,7 +58,7 @@ __global__ void __launch_bounds__(kWinThreads) k_window_bitmap(const uint8_t *__
     if (__syncthreads_or(timed_out)) return;
 
     const uint64_t p0 = tile + 32u * (uint64_t)t;
-    const uint32_t bits = clip_bits(window_bits32<W>(sbuf, t, wlen, mask, magic), p0, wlen, n);
+    const uint32_t bits = clip_bits(window_bits32<W>(sbuf, t, wlen, mask, magic, one), p0, wlen, n);
     const uint64_t nwords = (n + 31) / 32;
     const uint64_t widx = tile / 32 + t;
     if (widx < nwords) bitmap[widx] = bits;
@@ -76,7 +78,7 @@ void launch_window_t(const uint8_t *d_in, uint64_t n, uint32_t w, uint32_t mask,
                      uint32_t *d_bitmap, uint32_t *d_tile_cnt, uint64_t ntiles, cudaStream_t s,
                      int *d_err, uint32_t tile0) {
     k_window_bitmap<W><<<(unsigned)ntiles, kWinThreads, 0, s>>>(d_in, n, w, mask, magic, d_bitmap,
-                                                                 d_tile_cnt, d_err, tile0);
+                                                                 d_tile_cnt, d_err, tile0, 1u);
 }
 
 }  // namespace

@@ -12,6 +12,8 @@ namespace hg {
 constexpr int kHalo = 64;                              // >= window - 1, multiple of 16
 constexpr int kSmemBytes = kHalo + (int)kWinTile + 16; // + a zeroed 16-byte pad
 constexpr long kWaitLimit = 1L << 22;                  // bounded mbarrier polling
+// Pipe policies of the window hash's constant-word and data-word steps.
+constexpr uint32_t kWinPolConst = kPolAllPlain, kWinPolData = kPolAllPlain;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -31,9 +33,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
 
 // MD5 of one window given its data words d[] (little-endian, the last word may
 // carry bytes past the window, which are masked). Only word A of the final
-// state is formed: the window test reads the first four digest bytes.
-template <int W>
-__device__ __forceinline__ uint32_t window_a(const uint32_t (&d)[(W + 3) / 4]) {
+// state is formed: the window test reads the first four digest bytes. PC / PD
+// split the adds of the constant-word / data-word steps between the integer
+// ALU and FMA pipes (pipe policies in hg_device.cuh); `one` is a run-time 1.
+template <int W, uint32_t PC, uint32_t PD>
+__device__ __forceinline__ uint32_t window_a(const uint32_t (&d)[(W + 3) / 4], uint32_t one) {
     constexpr int NW = (W + 3) / 4;
     uint32_t M[16];
 #pragma unroll
@@ -47,20 +51,27 @@ __device__ __forceinline__ uint32_t window_a(const uint32_t (&d)[(W + 3) / 4]) {
         M[NW - 1] = (d[NW - 1] & keep) | (0x80u << (8 * (W % 4)));
     }
     M[14] = (uint32_t)W * 8u;                         // bit length, little-endian
-    uint32_t a = kMd5A, b = kMd5B, c = kMd5C, dd = kMd5D;
-    md5_rounds<false>(a, b, c, dd, M);
-    return a + kMd5A;
+    if constexpr (PC == kPolAllPlain && PD == kPolAllPlain) {
+        uint32_t a = kMd5A, b = kMd5B, c = kMd5C, dd = kMd5D;
+        md5_rounds<false>(a, b, c, dd, M);
+        return a + kMd5A;
+    } else {
+        // words 0 .. NW-1 carry window bytes; the rest are constants
+        uint32_t st[4] = {kMd5A, kMd5B, kMd5C, kMd5D};
+        md5_rounds_split<61, (1u << NW) - 1u, PC, PD>(st, M, one);
+        return st[0] + kMd5A;
+    }
 }
 
 // Window number S (0..6) of a group, counted in bytes from word cur[0].
-template <int W, int S>
-__device__ __forceinline__ uint32_t window_at(const uint32_t (&cur)[(W + 3) / 4 + 2]) {
+template <int W, int S, uint32_t PC, uint32_t PD>
+__device__ __forceinline__ uint32_t window_at(const uint32_t (&cur)[(W + 3) / 4 + 2], uint32_t one) {
     constexpr int NW = (W + 3) / 4, SH = S & 3, WO = S >> 2;
     uint32_t d[NW];
 #pragma unroll
     for (int k = 0; k < NW; k++)
         d[k] = SH == 0 ? cur[WO + k] : __funnelshift_r(cur[WO + k], cur[WO + k + 1], 8 * SH);
-    return window_a<W>(d);
+    return window_a<W, PC, PD>(d, one);
 }
 
 // Window hash for a window length known only at run time (any 1..55): the
@@ -112,9 +123,9 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mb, uint32_t parity) {
 // The 32 candidate bits of one thread: window ends [p0, p0 + 32) where p0 is
 // local byte kHalo + 32t of the staged tile sbuf (the tile starts kHalo bytes
 // before its first window end).
-template <int W>
+template <int W, uint32_t PC = kWinPolConst, uint32_t PD = kWinPolData>
 __device__ __forceinline__ uint32_t window_bits32(const uint8_t *sbuf, int t, uint32_t wlen,
-                                                  uint32_t mask, uint32_t magic) {
+                                                  uint32_t mask, uint32_t magic, uint32_t one) {
     constexpr int NW = W ? (W + 3) / 4 : 1;
     constexpr int OFF = kHalo - (W ? W - 1 : 0);      // local byte of window 0's start
     constexpr int B0 = OFF / 4, R0 = OFF % 4;
@@ -126,10 +137,10 @@ __device__ __forceinline__ uint32_t window_bits32(const uint8_t *sbuf, int t, ui
         for (int i = 0; i < NW + 2; i++) cur[i] = sw[8 * t + B0 + i];
 #pragma unroll 1
         for (int g = 0; g < 8; g++) {
-            const uint32_t h0 = window_at<W, R0 + 0>(cur);
-            const uint32_t h1 = window_at<W, R0 + 1>(cur);
-            const uint32_t h2 = window_at<W, R0 + 2>(cur);
-            const uint32_t h3 = window_at<W, R0 + 3>(cur);
+            const uint32_t h0 = window_at<W, R0 + 0, PC, PD>(cur, one);
+            const uint32_t h1 = window_at<W, R0 + 1, PC, PD>(cur, one);
+            const uint32_t h2 = window_at<W, R0 + 2, PC, PD>(cur, one);
+            const uint32_t h3 = window_at<W, R0 + 3, PC, PD>(cur, one);
             const uint32_t nib = (uint32_t)((h0 & mask) == magic) |
                                  ((uint32_t)((h1 & mask) == magic) << 1) |
                                  ((uint32_t)((h2 & mask) == magic) << 2) |
