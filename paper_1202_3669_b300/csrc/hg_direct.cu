@@ -28,11 +28,13 @@ __global__ void __launch_bounds__(128) k_hash_blocks(const uint8_t *__restrict__
 // constants.
 template <class H>
 __device__ __forceinline__ void hash_aligned_block(const uint8_t *__restrict__ in, uint64_t block,
-                                                   uint64_t i, uint8_t *__restrict__ out) {
+                                                   uint64_t i, uint8_t *__restrict__ out,
+                                                   uint32_t one) {
     const uint4 *p = reinterpret_cast<const uint4 *>(in + i * block);
     const uint64_t nb = block >> 6;
     H hs;
     hs.init();
+    hs.set_one(one);
     for (uint64_t k = 0; k < nb; k++) {
         const uint4 x0 = __ldg(p + 4 * k), x1 = __ldg(p + 4 * k + 1);
         const uint4 x2 = __ldg(p + 4 * k + 2), x3 = __ldg(p + 4 * k + 3);
@@ -46,15 +48,24 @@ __device__ __forceinline__ void hash_aligned_block(const uint8_t *__restrict__ i
     store_digest(hs, out + i * H::kDigest);
 }
 
-// Many blocks: the throughput form, capped at 32 registers so 2048 threads
-// fit an SM: with one chain per thread, occupancy is what hides the loads
-// (measured 4.1 vs 3.3 TB/s for the same loop at 37 registers).
+// Many blocks: the throughput form. MD5 is capped at 32 registers so 2048
+// threads fit an SM: with one chain per thread, occupancy is what hides the
+// loads (measured 4.1 vs 3.3 TB/s for the same loop at 37 registers). SHA-1
+// runs Sha1Split with pipe policy 3 (e + W on the FMA pipe) at 12 CTAs per SM
+// (40 registers, no spills): 1 GiB in 4 KiB blocks 0.534 -> 0.461 ms; at 16
+// CTAs per SM the same code spills.
+template <class H> struct AlignedForm { using Hash = H; static constexpr int kMinCtas = 16; };
+template <> struct AlignedForm<Sha1> {
+    using Hash = Sha1Split<0xFFFFu>;
+    static constexpr int kMinCtas = 12;
+};
+
 template <class H>
-__global__ void __launch_bounds__(128, 16) k_hash_blocks_aligned(const uint8_t *__restrict__ in,
-                                                                  uint64_t block, uint64_t nfull,
-                                                                  uint8_t *__restrict__ out) {
+__global__ void __launch_bounds__(128, AlignedForm<H>::kMinCtas)
+    k_hash_blocks_aligned(const uint8_t *__restrict__ in, uint64_t block, uint64_t nfull,
+                          uint8_t *__restrict__ out, uint32_t one) {
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < nfull) hash_aligned_block<H>(in, block, i, out);
+    if (i < nfull) hash_aligned_block<typename AlignedForm<H>::Hash>(in, block, i, out, one);
 }
 
 // Few blocks (fewer chains than it takes to fill the integer pipes): each
@@ -172,8 +183,8 @@ int launch_hash_blocks(int algo, const uint8_t *d_in, uint64_t n, uint64_t block
         const uint64_t nfull = n / block;
         if (nfull >= kFewChains) {
             const unsigned grid = (unsigned)((nfull + 127) / 128);
-            if (algo == HG_MD5) k_hash_blocks_aligned<Md5><<<grid, 128, 0, s>>>(d_in, block, nfull, d_digests);
-            else k_hash_blocks_aligned<Sha1><<<grid, 128, 0, s>>>(d_in, block, nfull, d_digests);
+            if (algo == HG_MD5) k_hash_blocks_aligned<Md5><<<grid, 128, 0, s>>>(d_in, block, nfull, d_digests, 1u);
+            else k_hash_blocks_aligned<Sha1><<<grid, 128, 0, s>>>(d_in, block, nfull, d_digests, 1u);
         } else if (nfull) {
             const uint32_t lanes = nfull <= kHalfWarpChainsMax ? 16 : 32;
             const unsigned grid = chain_grid(nfull, lanes, 64);

@@ -12,8 +12,15 @@ namespace hg {
 constexpr int kHalo = 64;                              // >= window - 1, multiple of 16
 constexpr int kSmemBytes = kHalo + (int)kWinTile + 16; // + a zeroed 16-byte pad
 constexpr long kWaitLimit = 1L << 22;                  // bounded mbarrier polling
-// Pipe policies of the window hash's constant-word and data-word steps.
-constexpr uint32_t kWinPolConst = kPolAllPlain, kWinPolData = kPolAllPlain;
+// Pipe policies of the window hash's constant-word and data-word steps: the
+// constant-word steps (42 of the 61) move both adds to the FMA pipe, the
+// data-word steps keep theirs on the ALU. Measured on a 64 MiB window pass
+// (ncu, 20-byte window): 0.688 -> 0.650 ms, ALU-pipe instructions per window
+// 191 -> 149, FMA-pipe 20 -> 104. Moving the data-word steps' adds as well, or
+// only the off-chain add, measured slower (0.66-0.71 ms): with both pipes
+// partly busy the kernel becomes issue- and dependency-limited (issue active
+// 70 %, math-pipe-throttle and barrier stalls).
+constexpr uint32_t kWinPolConst = kPolAll2, kWinPolData = kPolAllPlain;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -129,6 +136,9 @@ __device__ __forceinline__ uint32_t window_bits32(const uint8_t *sbuf, int t, ui
     constexpr int NW = W ? (W + 3) / 4 : 1;
     constexpr int OFF = kHalo - (W ? W - 1 : 0);      // local byte of window 0's start
     constexpr int B0 = OFF / 4, R0 = OFF % 4;
+    // the last thread's last word read stays inside the staged tile + zero pad
+    static_assert(W == 0 || 8 * (kWinThreads - 1) + B0 + 7 + NW + 2 < kSmemBytes / 4,
+                  "window words read past the staged tile");
     uint32_t bits = 0;
     if constexpr (W > 0) {
         const uint32_t *sw = reinterpret_cast<const uint32_t *>(sbuf);
