@@ -100,11 +100,18 @@ const char *hg_strerror(int s) {
         case HG_EAGAIN: return "not ready";
         case HG_ECANCELED: return "cancelled";
         case HG_EUNSUPPORTED: return "unsupported parameters";
+        case HG_EBOUNDS: return "debug bounds check failed";
         default: return "unknown status";
     }
 }
 
 int hg_digest_len(int algo) { return algo == HG_MD5 ? 16 : algo == HG_SHA1 ? 20 : HG_EINVAL; }
+
+int hg_host_digest(int algo, const uint8_t *msg, uint64_t n, uint8_t *out) {
+    if (hg_digest_len(algo) < 0 || !out || (n && !msg)) return HG_EINVAL;
+    host_digest(algo, msg, n, out);
+    return HG_OK;
+}
 
 int hg_init(hg_ctx **out, int device, size_t budget) {
     if (!out) return HG_EINVAL;
@@ -145,6 +152,7 @@ int hg_destroy(hg_ctx *c) {
     cudaFree(c->d_tasks);
     cudaFree(c->d_err);
     pinned_destroy(c);
+    if (c->root_stage) cudaFreeHost(c->root_stage);
     if (c->pipe_ready) {
         if (c->p_exec) cudaGraphExecDestroy(c->p_exec);
         cudaStreamDestroy(c->p_cap);
@@ -196,9 +204,18 @@ int hg_hash_blocks(hg_ctx *c, int algo, const uint8_t *d_in, uint64_t n, uint64_
     DeviceGuard g(c->device);
     cudaStream_t s = (cudaStream_t)stream;
     int r = launch_hash_blocks(algo, d_in, n, block, d_digests, s, c->d_err);
-    if (r) return r;
-    if (d_root) r = launch_root(algo, d_digests, nblk * (uint64_t)hg_digest_len(algo), d_root, s);
-    return r;
+    if (r || !d_root) return r;
+    // The hash-of-hashes is one serial chain: on a host core (Sec. 3.2.2 computes
+    // it on the CPU) unless the list is tiny or the stream is being captured.
+    const uint64_t nbytes = nblk * (uint64_t)hg_digest_len(algo);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusActive;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        cs = cudaStreamCaptureStatusActive;
+    }
+    if (nbytes >= host_root_min_bytes() && cs == cudaStreamCaptureStatusNone)
+        return enqueue_host_root(c, algo, d_digests, nbytes, d_root, s);
+    return launch_root(algo, d_digests, nbytes, d_root, s);
 }
 
 int hg_hash_blocks_pmd(hg_ctx *c, int algo, const uint8_t *d_in, uint64_t n, uint64_t block,
@@ -404,7 +421,7 @@ static int enqueue_cdc_hash(hg_ctx *c, int algo, const uint8_t *d_in, uint64_t n
                                      h_in ? c->p_ev_copy[k] : nullptr, !defer)))
             return r;
     }
-    if (defer && (r = launch_hash_sorted(d_in, n / p->min_chunk + 2, *p, algo, pb, c->p_sel)))
+    if (defer && (r = launch_hash_sorted(d_in, n, n / p->min_chunk + 2, *p, algo, pb, c->p_sel)))
         return r;
     cudaEventRecord(c->p_done_sel, c->p_sel);
     cudaStreamWaitEvent(s, c->p_done_sel, 0);

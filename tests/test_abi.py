@@ -90,3 +90,22 @@ def test_pinned_size_classes_and_null_context():
         assert n <= c <= max(64 << 10, n + n // 4 + 1)
     assert L.hg_alloc_pinned(None, 100) is None
     assert L.hg_free_pinned(None, None) == _lib.HG_EINVAL
+
+
+def test_host_digest_equals_hashlib():
+    """The library's host MD5/SHA-1 (used for the hash-of-hashes) against OpenSSL via
+    hashlib at every length 0..1100 and on a MiB-sized input; no device needed."""
+    import hashlib
+
+    import numpy as np
+
+    from paper_1202_3669_b300 import _lib
+    g = np.random.default_rng(7)
+    buf = g.integers(0, 256, (1 << 20) + 77, dtype=np.uint8)
+    out = np.zeros(20, np.uint8)
+    for algo, ref, dl in ((0, hashlib.md5, 16), (1, hashlib.sha1, 20)):
+        for n in list(range(0, 1101)) + [buf.size]:
+            assert _lib.lib.hg_host_digest(algo, buf.ctypes.data if n else None, n,
+                                           out.ctypes.data) == 0
+            assert out[:dl].tobytes() == ref(buf[:n].tobytes()).digest(), (algo, n)
+    assert _lib.lib.hg_host_digest(7, None, 0, out.ctypes.data) == _lib.HG_EINVAL
