@@ -46,15 +46,23 @@ METRIC = "hashed GB/s (CDC: 20-byte MD5 window + min/max boundaries + per-chunk 
 # same kernels without segment pipelining) is reported beside it.
 UNIT = "GB/s"
 WORKLOAD = "cdc_64MiB_base_plus_1pct_edited_version"
-# Algorithmic cost of one window hash in integer-ALU instructions (3-input logic op,
-# 3-input add and the rotate-add each count one): 42 operations with a constant
-# message word x 3 + 19 with a data word x 4, + 3.75 funnel shifts to assemble
-# the window, + 4 for the test and bit collection = 208 (ncu counted 194 ALU-pipe + 10
-# FMA-pipe instructions per window).
-ALU_OPS_PER_WINDOW = 208
-ALU_LANES_PER_SM_CLK = 64     # integer ALU pipe: one warp instruction per 2 clocks per scheduler
-TWO_INPUT_OPS_PER_WINDOW = 270  # the same work counted in 2-input operations
-ISSUE_LANES_PER_SM_CLK = 128  # 4 schedulers x 32 lanes
+# Algorithmic cost of one window hash in two-input 32-bit integer operations (the
+# roofline unit): one MD5 compression per window; 44 steps whose message word is a
+# constant fold it with the step constant (4 operations), the steps on data words take
+# 5, the hash stops after the step that last writes word A, and the window assembly
+# (funnel shifts) and the candidate test add about 8: about 270 per window (one per
+# input byte). Against the integer issue rate (4 schedulers x 32 lanes per SM per
+# clock); a kernel could pass 1.0 only by fusing two-input operations into three-input
+# instructions beyond what the count assumes.
+OPS_PER_WINDOW = 270
+ISSUE_LANES_PER_SM_CLK = 128
+# Per-chunk MD5 adds about 5.1 operations per byte (64 steps x 5 + 4 final adds per
+# 64 bytes), so the whole chunking step costs about 275 operations per input byte.
+OPS_PER_BYTE_CDC_STEP = OPS_PER_WINDOW + 5.1
+OPS_PER_BYTE_MD5, OPS_PER_BYTE_SHA1 = 5.1, 9.6
+# The integer ALU pipe alone (logic, funnel shift, rotate-add issue only there) takes
+# one warp instruction every other clock per scheduler: 64 lanes per SM per clock.
+ALU_LANES_PER_SM_CLK = 64
 # the window kernel's own sources: its counters in profiles/ hold only while these are unchanged
 WINDOW_KERNEL_SRC = [os.path.join(ROOT, "paper_1202_3669_b300", "csrc", f)
                      for f in ("hg_window.cu", "hg_window.cuh", "hg_device.cuh")]
@@ -175,9 +183,57 @@ def kernel_traffic(kernel: str, srcs):
     return rec
 
 
+def cpu_info() -> dict:
+    """Host CPU model and the threads the oracle baselines use."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"model": model, "nproc": os.cpu_count() or 1}
+
+
+def _threads_map(fn, items, nthreads):
+    import concurrent.futures as cf
+    with cf.ThreadPoolExecutor(nthreads) as ex:
+        return list(ex.map(fn, items))
+
+
+def _oracle_blocks_n(oracle, L, algo, data, block, nthreads):
+    """Fixed-block digests + root with the oracle, blocks split over threads (each
+    thread one contiguous range of whole blocks); the root hashes the digest list."""
+    nblk = (data.size + block - 1) // block
+    cuts = np.linspace(0, nblk, min(nblk, nthreads) + 1).astype(np.int64)
+    parts = _threads_map(lambda k: oracle.hash_blocks(algo, data[cuts[k] * block:cuts[k + 1] * block],
+                                                      block, root=False, L=L)[0],
+                         range(cuts.size - 1), nthreads)
+    dg = np.concatenate(parts)
+    return dg, oracle.digest(algo, dg.tobytes(), L=L)
+
+
+def _time_rate(fn, nbytes, reps=3):
+    """Wall-clock median of reps runs."""
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        fn()
+        ts.append(time.perf_counter() - t0)
+    dt = statistics.median(ts)
+    return {"GBps": nbytes / dt / 1e9, "seconds": dt, "bytes": int(nbytes), "runs": reps}
+
+
 def cpu_baseline(versions, budget_s: float = 12.0):
-    """The oracle as it stands, on the host cores, on a bounded sample of the workload."""
+    """The oracle as it stands, on the host cores, on bounded samples of each
+    configuration: the main chunking workload on all threads (the headline baseline) and
+    on one thread, plus the 8 MiB fixed-block configuration, fixed blocks and chunking of
+    the 1 GiB inputs (samples), each on one thread and fanned out over all threads
+    (independent block ranges; window ranges inside the oracle)."""
     import oracle
+    from gen import inputs as G
     nthreads = os.cpu_count() or 1
     L = oracle.lib()
     # calibrate on growing prefixes (thread start-up dominates tiny probes), then size the
@@ -211,8 +267,37 @@ def cpu_baseline(versions, budget_s: float = 12.0):
     dt1 = time.perf_counter() - t1
     single = {"value": 2 * n1 / dt1 / 1e9, "unit": UNIT, "cores": 1, "seconds": dt1,
               "sample": f"first {n1} bytes of each version"}
+
+    # the other configurations, on samples sized from the rates above
+    configs = {}
+    c1 = G.uniform_bytes(8 << 20, seed=1)
+    for algo, name in ((oracle.MD5, "md5"), (oracle.SHA1, "sha1")):
+        configs[f"c1_8MiB_4KiB_{name}_with_root"] = {
+            "1_thread": _time_rate(lambda: oracle.hash_blocks(algo, c1, 4096, L=L), c1.size),
+            f"{nthreads}_threads": _time_rate(lambda: _oracle_blocks_n(oracle, L, algo, c1, 4096, nthreads),
+                                              c1.size)}
+    u = G.uniform_bytes(64 << 20, seed=4)          # a 64 MiB sample drawn as the 1 GiB input is
+    for algo, name in ((oracle.MD5, "md5"), (oracle.SHA1, "sha1")):
+        for block, label in ((4096, "4KiB"), (1 << 20, "1MiB")):
+            configs[f"c3_uniform_{label}_{name}"] = {
+                "1_thread": _time_rate(lambda: oracle.hash_blocks(algo, u[:16 << 20], block, L=L), 16 << 20),
+                f"{nthreads}_threads": _time_rate(
+                    lambda: _oracle_blocks_n(oracle, L, algo, u, block, nthreads), u.size)}
+    ncdc = int(min(16 << 20, max(1 << 20, rate * budget_s / 8)))
+    n1c = int(max(1 << 17, n1 // 4))
+    t = G.text_like_bytes(ncdc, seed=5)
+    for dist, data in (("uniform", u[:ncdc]), ("text", t)):
+        def cdc_all(d=data):
+            e = oracle.cdc(d, nthreads=nthreads, L=L)
+            oracle.hash_chunks(oracle.MD5, d, e, L=L)
+
+        def cdc_one(d=data[:n1c]):
+            e = oracle.cdc(d, nthreads=1, L=L)
+            oracle.hash_chunks(oracle.MD5, d, e, L=L)
+        configs[f"c3_{dist}_cdc_md5"] = {"1_thread": _time_rate(cdc_one, n1c),
+                                         f"{nthreads}_threads": _time_rate(cdc_all, data.size)}
     return {"value": total / dt / 1e9, "unit": UNIT, "cores": nthreads, "kind": "oracle",
-            "single_thread": single,
+            "single_thread": single, "cpu": cpu_info(), "configs": configs,
             "sample": f"first {nbytes} bytes of each of the two versions ({total} bytes), "
                       f"window candidates on {nthreads} threads + selection + per-chunk MD5",
             "seconds": dt}
@@ -289,9 +374,10 @@ def main():
         elif args.leg == "configs":
             res = configs_leg(hgb, ctx, dev, flush)
         elif args.leg == "alu":
-            res = alu_leg(hgb, ctx, dev)
+            res = alu_leg(dev)
         else:
-            res = serve_leg(hgb, ctx, batch_leg(hgb, ctx, dev, flush)["batched_graph_GBps"])
+            bl = batch_leg(hgb, ctx, dev, flush)
+            res = serve_leg(hgb, ctx, bl["batched_graph_GBps"], bl["per_file_GBps"])
         print(json.dumps({"leg": args.leg, "result": res}), flush=True)
         return
     versions = workload()
@@ -373,11 +459,23 @@ def main():
     torch.cuda.synchronize()
     t_two = sum(a.elapsed_time(b) for a, b in tw) / len(tw)
 
-    # e2e: pinned host inputs -> device -> boundaries + digests -> pinned host
-    h_in = [torch.from_numpy(v).pin_memory() for v in versions]
-    h_ends = [torch.empty(c, dtype=torch.int64).pin_memory() for c in cap]
-    h_cnt = [torch.empty(1, dtype=torch.int64).pin_memory() for _ in versions]
-    h_dg = [torch.empty((c, 16), dtype=torch.uint8).pin_memory() for c in cap]
+    # e2e: pinned host inputs -> device -> boundaries + digests -> pinned host; the pinned
+    # buffers come from the library's pool (hg_alloc_pinned)
+    def pinned(ctx, nbytes, dtype, shape):
+        b = ctx.alloc_pinned(nbytes)
+        return b, b.tensor.view(dtype)[:int(np.prod(shape))].view(shape)
+    pool = []
+    h_in, h_ends, h_cnt, h_dg = [], [], [], []
+    for i, v in enumerate(versions):
+        b, t = pinned(ctxs[i], v.size, torch.uint8, (v.size,))
+        t.numpy()[:] = v
+        pool.append(b)
+        h_in.append(t)
+        for lst, nb, dt, shp in ((h_ends, cap[i] * 8, torch.int64, (cap[i],)), (h_cnt, 8, torch.int64, (1,)),
+                                 (h_dg, cap[i] * 16, torch.uint8, (cap[i], 16))):
+            b, t = pinned(ctxs[i], nb, dt, shp)
+            pool.append(b)
+            lst.append(t)
     d_in2 = [torch.empty_like(x) for x in d_in]
     h2d = sum(v.size for v in versions)
     d2h = sum(e.numel() * 8 + 8 + d.numel() for e, d in zip(h_ends, h_dg))
@@ -421,6 +519,7 @@ def main():
         ev.append((a, b))
     torch.cuda.synchronize()
     t_e2e = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
+    pool_stats = [c.pinned_stats() for c in ctxs]
     clocks = clk.stop()
     for c in ctxs:
         c.sync()
@@ -448,23 +547,35 @@ def main():
     peaks, peak_kind = measured_peaks()
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_max = float(peaks.get("sm_max_mhz", 2032.0))
-    peak_tops = sm_count * ALU_LANES_PER_SM_CLK * sm_max * 1e6 / 1e12
-    achieved = windows * ALU_OPS_PER_WINDOW / t_win / 1e12
     issue_peak = sm_count * ISSUE_LANES_PER_SM_CLK * sm_max * 1e6 / 1e12
+    alu_peak = sm_count * ALU_LANES_PER_SM_CLK * sm_max * 1e6 / 1e12
+    achieved = windows * OPS_PER_WINDOW / t_win / 1e12
     tr = kernel_traffic("k_window_bitmap", WINDOW_KERNEL_SRC)
+    counters = (tr or {}).get("per_window", {})
     roofline = {"bound": "alu", "kernel": "k_window_bitmap<20>", "achieved": achieved,
-                "peak": peak_tops, "unit": "Tops/s (int32 ALU-pipe instructions)",
-                "frac": achieved / peak_tops,
-                "peak_kind": f"{sm_count} SMs x {ALU_LANES_PER_SM_CLK} lanes/clk (integer ALU pipe) x "
-                             f"{sm_max:.0f} MHz (max SM clock, {peak_kind} clock); recipe unit counts",
-                "ops_per_window": ALU_OPS_PER_WINDOW, "windows_per_launch": windows,
+                "peak": issue_peak, "unit": "Tops/s (two-input int32 operations)",
+                "frac": achieved / issue_peak,
+                "peak_kind": (f"int32 issue rate: {sm_count} SMs x {ISSUE_LANES_PER_SM_CLK} lanes/clk x "
+                              f"{sm_max:.0f} MHz (max SM clock, {peak_kind} clock); algorithmic count "
+                              f"{OPS_PER_WINDOW} two-input operations per window"),
+                "ops_per_window": OPS_PER_WINDOW, "windows_per_launch": windows,
                 "launch_ms": t_win * 1e3, "window_GBps": versions[0].size / t_win / 1e9,
-                "frac_two_input_count_vs_issue_peak": windows * TWO_INPUT_OPS_PER_WINDOW / t_win / 1e12 / issue_peak,
                 "traffic": (tr["dram_bytes_per_launch"] * versions[0].size / tr["input_bytes"]) if tr else None}
+    if counters.get("alu_pipe_inst"):
+        # secondary: the instructions ncu counted on each pipe, against each pipe's peak
+        roofline["alu_pipe_frac"] = windows * counters["alu_pipe_inst"] / t_win / 1e12 / alu_peak
+        roofline["issue_frac"] = windows * counters["all_inst"] / t_win / 1e12 / issue_peak
+        roofline["counted_per_window"] = counters
     if clocks.get("sm_mhz"):
-        roofline["frac_at_observed_clock"] = achieved / (peak_tops * clocks["sm_mhz"] / sm_max)
-    # the integer pipe's rate measured by a probe (per operation class), beside the peak used
-    roofline["measured_int_pipe"] = alu_leg(hgb, ctxs[0], dev)
+        roofline["frac_at_observed_clock"] = achieved / (issue_peak * clocks["sm_mhz"] / sm_max)
+    # the integer pipes' rates measured by the probe (per operation class), beside the peak used
+    roofline["measured_int_pipe"] = alu_leg(dev)
+    # the whole chunking step (windows + selection + per-chunk MD5) against its bound
+    step_bound = issue_peak * 1e12 / OPS_PER_BYTE_CDC_STEP / 1e9
+    cdc_step_roofline = {"bound": "alu", "achieved": nbytes / (t_dev / 1e3) / 1e9,
+                         "peak": step_bound, "unit": "GB/s",
+                         "frac": nbytes / (t_dev / 1e3) / 1e9 / step_bound,
+                         "peak_kind": f"int32 issue rate / {OPS_PER_BYTE_CDC_STEP:.1f} operations per byte"}
 
     # shared-chunk fraction between the versions (from this run's device results)
     k0, k1 = int(cnts[0].item()), int(cnts[1].item())
@@ -480,7 +591,8 @@ def main():
         extras["blockmap"] = blockmap_leg(hgb, ctxs[0], dev, flush)
         extras["configs"] = configs_leg(hgb, ctxs[0], dev, flush)
         extras["batch"] = batch_leg(hgb, ctxs[0], dev, flush)
-        extras["serve"] = serve_leg(hgb, ctxs[0], extras["batch"]["batched_graph_GBps"])
+        extras["serve"] = serve_leg(hgb, ctxs[0], extras["batch"]["batched_graph_GBps"],
+                                    extras["batch"]["per_file_GBps"])
         extras["cpu_baseline"] = cpu_baseline(versions)
 
     # max over ranks
@@ -500,9 +612,13 @@ def main():
                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                "e2e": {"value": replica_throughput(nbytes, world, t_e2e_all), "unit": UNIT,
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                       "pinned_h2d_copy_GBps": h2d_gbps},
+                       "pinned_h2d_copy_GBps": h2d_gbps,
+                       "pinned_from": "hg_alloc_pinned pool",
+                       "pinned_pool": {"host_allocs": sum(x["host_allocs"] for x in pool_stats),
+                                       "held_bytes": sum(x["held_bytes"] for x in pool_stats)}},
                "gpu_launches": launches_per_step * args.steps,
                "roofline": roofline,
+               "cdc_step_roofline": cdc_step_roofline,
                "cpu_baseline": extras.get("cpu_baseline"),
                "clocks": clocks,
                "step_ms_p50": statistics.median(step_ms), "step_ms_max": max(step_ms),
@@ -543,15 +659,31 @@ def direct_leg(hgb, ctx, dev, flush):
         return {"GBps": (1 << 30) / t / 1e9, "ms": t * 1e3,
                 "hbm_frac": (1 << 30) / t / 1e9 / peaks["hbm_gbs"]}
 
+    # bound of a fixed-block digest: min(HBM, int32 issue rate / operations per byte)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    issue = sms * ISSUE_LANES_PER_SM_CLK * float(peaks.get("sm_max_mhz", 2032.0)) * 1e6
+
+    def with_bound(r, ops_per_byte):
+        alu = issue / ops_per_byte / 1e9
+        bound = min(peaks["hbm_gbs"], alu)
+        r["roofline"] = {"bound": "hbm" if peaks["hbm_gbs"] <= alu else "alu", "peak_GBps": bound,
+                         "frac": r["GBps"] / bound}
+        return r
+
     for algo, name in ((hgb.MD5, "md5"), (hgb.SHA1, "sha1")):
         dl = 16 if algo == hgb.MD5 else 20
         out = torch.empty(((1 << 30) // 4096, dl), dtype=torch.uint8, device=dev)
         rt = torch.empty(dl, dtype=torch.uint8, device=dev)
+        opb = OPS_PER_BYTE_MD5 if algo == hgb.MD5 else OPS_PER_BYTE_SHA1
         for block, label in ((4096, "4KiB"), (65536, "64KiB"), (1 << 20, "1MiB")):
-            res[f"{name}_{label}"] = timed(
-                lambda: ctx.hash_blocks(data, block, algo, root=False, out=out))
-        res[f"{name}_4KiB_with_root"] = timed(
-            lambda: ctx.hash_blocks(data, 4096, algo, root=True, out=out, root_out=rt), reps=5, warm=2)
+            res[f"{name}_{label}"] = with_bound(timed(
+                lambda: ctx.hash_blocks(data, block, algo, root=False, out=out)), opb)
+        r = timed(lambda: ctx.hash_blocks(data, 4096, algo, root=True, out=out, root_out=rt),
+                  reps=5, warm=2)
+        r["root_ms"] = r["ms"] - res[f"{name}_4KiB"]["ms"]
+        r["root_share"] = r["root_ms"] / r["ms"]
+        r["root_note"] = "hash-of-hashes over 4 MiB (MD5) / 5 MiB (SHA-1) of digests on a host core"
+        res[f"{name}_4KiB_with_root"] = r
         ids = torch.empty(((1 << 30) >> 20, dl), dtype=torch.uint8, device=dev)
         res[f"{name}_1MiB_two_level_4KiB"] = timed(
             lambda: ctx.hash_blocks_pmd(data, 1 << 20, 4096, algo, out=ids, seg_out=out))
@@ -561,29 +693,49 @@ def direct_leg(hgb, ctx, dev, flush):
     return res
 
 
-def alu_leg(hgb, ctx, dev, iters=65536):
-    """Integer-pipe throughput probe (hg_probe_int_pipe): 8 CTAs x 256 threads per SM, 8
-    independent chains per thread, per operation class; lanes per clock per SM at the
-    maximum SM clock (the clock the bench runs at, sampled alongside)."""
+def probe_lib():
+    """The benchmark's integer-pipe probe library (built beside its source)."""
+    import ctypes as C
+    path = os.path.join(ROOT, "paper_1202_3669_b300", "bench_probe", "libhgprobe.so")
+    if not os.path.exists(path):
+        import importlib.util
+        spec = importlib.util.spec_from_file_location(
+            "_hg_build", os.path.join(ROOT, "paper_1202_3669_b300", "build.py"))
+        mod = importlib.util.module_from_spec(spec)
+        spec.loader.exec_module(mod)
+        mod.build_probe()
+    lib = C.CDLL(path)
+    lib.hgp_probe_int_pipe.argtypes = [C.c_int, C.c_int, C.c_uint32, C.c_uint32, C.c_void_p, C.c_void_p]
+    return lib
+
+
+def alu_leg(dev, iters=65536):
+    """Integer-pipe throughput probe: 8 CTAs x 256 threads per SM, 8 independent chains per
+    thread, per operation class; lanes per clock per SM at the maximum SM clock (the clock
+    the bench runs at, sampled alongside)."""
+    import ctypes as C
+
     import torch
+    lib = probe_lib()
     s = torch.cuda.current_stream(dev)
     peaks, _ = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2032.0))
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     out = {}
-    for kind, name in ((0, "lop3"), (1, "iadd3"), (2, "shf_funnel"), (3, "md5_op_mix")):
+    ops = C.c_uint64()
+    for kind, name in ((0, "lop3"), (1, "iadd3"), (2, "shf_funnel"), (3, "md5_op_mix"),
+                       (4, "mad_by_runtime_1")):
         ts = []
         for i in range(5):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(s)
-            ops = ctx.probe_int_pipe(kind, iters, 8, stream=s)
+            assert lib.hgp_probe_int_pipe(dev.index or 0, kind, iters, 8, C.byref(ops), s.cuda_stream) == 0
             b.record(s)
             if i >= 2:
                 ts.append((a, b))
         torch.cuda.synchronize()
         t = statistics.median(x.elapsed_time(y) for x, y in ts) / 1e3
-        out[name] = {"Tops": ops / t / 1e12, "lanes_per_sm_clk": ops / t / (sms * sm_max * 1e6)}
-    ctx.sync()
+        out[name] = {"Tops": ops.value / t / 1e12, "lanes_per_sm_clk": ops.value / t / (sms * sm_max * 1e6)}
     out["note"] = f"{sms} SMs at {sm_max:.0f} MHz; md5_op_mix counts 4 ops per MD5-like step"
     return out
 
@@ -833,25 +985,33 @@ def batch_leg(hgb, ctx, dev, flush, nfiles=4096):
             "note": "per-file: hg_cdc_boundaries + hg_hash_chunks per file on one stream"}
 
 
-def serve_leg(hgb, ctx, capacity_gbps, fracs=(0.1, 0.4, 0.7, 1.0, 1.2), max_req=20000,
-              seconds=2.5):
-    """Open-loop Poisson arrivals at fractions of the batched capacity; request sizes log-normal
-    as in the batch workload; 70 % chunking + MD5, 30 % 64 KiB-block SHA-1 with root; 32 GiB
-    device budget. Payloads come from a 1 GiB pinned pool (request i reads a seeded slice);
-    latency is completion minus scheduled arrival."""
+def serve_leg(hgb, ctx, capacity_gbps, per_file_gbps=None, fracs=(0.1, 0.4, 0.7, 1.0, 1.2),
+              max_req=20000, seconds=2.5):
+    """Open-loop Poisson arrivals; request sizes log-normal as in the batch workload; 70 %
+    chunking + MD5, 30 % 64 KiB-block SHA-1 with root; 32 GiB device budget. Payloads come
+    from a 1 GiB buffer of the library's pinned pool (request i reads a seeded slice);
+    latency is completion minus scheduled arrival.
+
+    Two sweeps: the five rates as fractions of the batched capacity (device-resident
+    batch, the configuration's definition), and the same fractions of the served ceiling
+    (the throughput the server sustains when offered more than it can take, which the
+    host link bounds). p99 is reported for each; `p99_at_3x` is the p99 at the highest
+    rate that is sustained (achieved >= 95 % of offered) at >= 3x the per-file-launch
+    throughput."""
     import torch
     from gen import inputs as G
     pool_bytes = 1 << 30
-    pool = torch.from_numpy(G.uniform_bytes(pool_bytes, seed=77)).pin_memory()
-    base = pool.data_ptr()
     sctx = hgb.Context(ctx.device.index, budget=40 << 30)      # the server's own context
+    pbuf = sctx.alloc_pinned(pool_bytes)
+    pbuf.numpy()[:] = G.uniform_bytes(pool_bytes, seed=77)
+    base = pbuf.ptr
     srv = hgb.Server(sctx, device_budget=32 << 30, max_wave_bytes=1 << 30)
-    out = {"capacity_GBps": capacity_gbps, "budget_bytes": 32 << 30, "rates": []}
     sizes_all = G.lognormal_sizes(200000, seed=78)
     mean_size = float(sizes_all.mean())
-    for k, frac in enumerate(fracs):
-        lam = frac * capacity_gbps * 1e9 / mean_size
-        n = int(min(max_req, max(200, lam * seconds)))
+
+    def run(rate_gbps, k, secs=seconds):
+        lam = rate_gbps * 1e9 / mean_size
+        n = int(min(max_req, max(200, lam * secs)))
         g = G.rng(80 + k)
         sizes = G.lognormal_sizes(n, seed=90 + k)
         offs = (g.random(n) * (pool_bytes - sizes)).astype(np.int64)
@@ -870,13 +1030,35 @@ def serve_leg(hgb, ctx, capacity_gbps, fracs=(0.1, 0.4, 0.7, 1.0, 1.2), max_req=
         lat, span = srv.replay(reqs, arrivals)
         lat_ms = lat.astype(np.float64) / 1e6
         total = int(sizes.sum())
-        out["rates"].append({"frac": frac, "requests": n, "offered_GBps": total / (arrivals[-1] / 1e9) / 1e9,
-                             "achieved_GBps": total / (span / 1e9) / 1e9,
-                             "p50_ms": float(np.percentile(lat_ms, 50)),
-                             "p99_ms": float(np.percentile(lat_ms, 99)),
-                             "mean_request_bytes": total / n})
+        return {"requests": n, "offered_GBps": total / (arrivals[-1] / 1e9) / 1e9,
+                "achieved_GBps": total / (span / 1e9) / 1e9,
+                "p50_ms": float(np.percentile(lat_ms, 50)),
+                "p99_ms": float(np.percentile(lat_ms, 99)),
+                "mean_request_bytes": total / n}
+
+    out = {"capacity_GBps": capacity_gbps, "budget_bytes": 32 << 30, "rates": []}
+    for k, frac in enumerate(fracs):
+        out["rates"].append({"frac": frac, "of": "batched capacity", **run(frac * capacity_gbps, k)})
+    # the served ceiling: offered twice the batched capacity, what the server sustains
+    sat = run(2.0 * capacity_gbps, 20, secs=1.5)
+    ceiling = sat["achieved_GBps"]
+    out["served_ceiling_GBps"] = ceiling
+    out["rates_vs_served_ceiling"] = []
+    for k, frac in enumerate(fracs):
+        out["rates_vs_served_ceiling"].append({"frac": frac, "of": "served ceiling",
+                                               **run(frac * ceiling, 10 + k)})
+    if per_file_gbps:
+        ok = [r for r in out["rates"] + out["rates_vs_served_ceiling"]
+              if r["achieved_GBps"] >= 0.95 * r["offered_GBps"] and r["achieved_GBps"] >= 3 * per_file_gbps]
+        if ok:
+            best = max(ok, key=lambda r: r["achieved_GBps"])
+            out["p99_at_3x"] = {"achieved_GBps": best["achieved_GBps"], "p99_ms": best["p99_ms"],
+                                "p50_ms": best["p50_ms"], "per_file_GBps": per_file_gbps,
+                                "ratio_to_per_file": best["achieved_GBps"] / per_file_gbps}
     out["waves"] = srv.stats()["waves"]
+    out["pinned_pool"] = sctx.pinned_stats()
     srv.close()
+    pbuf.free()
     sctx.close()
     return out
 

@@ -51,7 +51,8 @@ typedef enum {
     HG_ECUDA = -5,        /* a CUDA runtime call failed */
     HG_EAGAIN = -6,       /* asynchronous result not ready yet */
     HG_ECANCELED = -7,    /* request cancelled before it ran */
-    HG_EUNSUPPORTED = -8  /* parameters outside what this build supports */
+    HG_EUNSUPPORTED = -8, /* parameters outside what this build supports */
+    HG_EBOUNDS = -9       /* debug build only: a kernel's bounds check failed */
 } hg_status;
 
 typedef enum { HG_MD5 = 0, HG_SHA1 = 1 } hg_algo;
@@ -101,6 +102,15 @@ const char *hg_strerror(int status);
 
 /* Digest length in bytes of algo (16, 20), or HG_EINVAL. */
 int hg_digest_len(int algo);
+
+/*
+ * The library's host-side digest (MD5 or SHA-1 of n bytes at msg into out,
+ * standard byte order), synchronous, on the calling thread; no device is
+ * needed. hg_hash_blocks computes the hash-of-hashes with it on a host core,
+ * as the paper does (Sec. 3.2.2: the CPU computes the final hash over the
+ * intermediate digests). HG_EINVAL for a bad algo or null pointers.
+ */
+int hg_host_digest(int algo, const uint8_t *msg, uint64_t n, uint8_t *out);
 
 /*
  * Create a context on CUDA device `device`. `device_budget_bytes` caps the
@@ -166,7 +176,13 @@ uint64_t hg_pinned_class(uint64_t bytes);
  * If d_root is not NULL it receives the hash-of-hashes: the digest, with the
  * same algorithm, of the nblk*dlen digest bytes in block order (Sec. 3.2.2,
  * the final step that hashes the buffer of intermediate digests). n = 0 gives
- * no blocks and the digest of the empty string as root.
+ * no blocks and the digest of the empty string as root. That final step is
+ * one serial chain; as in the paper it runs on a host core: the digests are
+ * copied to a pinned staging buffer of the context, hashed by a host function
+ * enqueued on `stream`, and the root is copied back, all in stream order
+ * (the staging buffer grows on demand, which synchronises the device once).
+ * Digest lists under 8 KiB, and calls made while `stream` is being captured
+ * into a CUDA graph, use a single-thread device kernel instead.
  * d_in: n bytes, any alignment. d_digests: nblk*dlen bytes, 4-byte aligned.
  * d_root: dlen bytes or NULL. Errors: HG_EINVAL (block == 0, bad algo,
  * null or misaligned buffer).
@@ -345,6 +361,16 @@ int hg_batch_set_tuning(hg_batch *batch, const hg_batch_tuning *tuning);
  * 60 times) and keep the fastest; it is also written to *best if not NULL. */
 int hg_batch_autotune(hg_batch *batch, int algo, const uint8_t *d_data, uint64_t *d_ends,
                       uint64_t *d_counts, uint8_t *d_digests, void *stream, hg_batch_tuning *best);
+/* hg_batch_autotune through a cache file (JSON Lines, one
+ * {"key": {...}, "tuning": {...}} object per line) keyed by the GPU name and SM
+ * count, the algorithm, the chunking parameters and the batch's shape (file
+ * count, log2 of its bytes, files of 1 MiB and more): a matching line sets the
+ * tuning without running anything (*from_cache = 1); otherwise the batch is
+ * tuned and a line is appended (*from_cache = 0). An unwritable file only
+ * skips the append. HG_EINVAL if cache_path is NULL. */
+int hg_batch_autotune_cached(hg_batch *batch, int algo, const uint8_t *d_data, uint64_t *d_ends,
+                             uint64_t *d_counts, uint8_t *d_digests, void *stream,
+                             const char *cache_path, hg_batch_tuning *best, int *from_cache);
 
 /*
  * Request server with continuous batching (Sec. 3.2.3: applications submit
@@ -430,19 +456,6 @@ int hg_server_replay(hg_server *srv, const hg_request *reqs, const uint64_t *arr
                      uint32_t nreq, uint64_t *latency_ns, uint64_t *span_ns);
 
 /*
- * Integer-pipe throughput probe (a measurement utility; the paper has no
- * counterpart): launches, on stream, ctas_per_sm (1..8) CTAs of 256 threads
- * per SM, each thread running 8 independent chains of `iters` operations of
- * one class -- kind 0: 3-input logic (lop3), 1: 3-input add, 2: funnel
- * shift, 3: the MD5 operation mix (logic, 3-input add, rotate, add: 4 ops).
- * *ops_out receives the number of operations the launch performs; time the
- * launch on the stream and divide by time x SMs x clock for lanes per clock
- * per SM, the peak of the integer rooflines.
- */
-int hg_probe_int_pipe(hg_ctx *ctx, int kind, uint32_t iters, uint32_t ctas_per_sm,
-                      uint64_t *ops_out, void *stream);
-
-/*
  * Device block map: similarity detection by digests (Sec. 2.1: identical
  * blocks have equal identifiers; Sec. 4.3: the share of a new version found in
  * chunks already stored). A hash table of distinct digests (algo fixes the
@@ -476,6 +489,20 @@ int hg_blockmap_lookup(hg_blockmap *map, const uint8_t *d_digests, const uint64_
 int hg_blockmap_count(hg_blockmap *map, uint64_t *d_out, void *stream);
 int hg_blockmap_clear(hg_blockmap *map, void *stream);
 int hg_blockmap_destroy(hg_blockmap *map);
+/*
+ * Bounded wait of hg_blockmap_insert: an insert that meets a slot claimed by
+ * another insert of the same tag polls that slot's publish word at most
+ * `polls` times (0 restores the default, 2^20) before it gives up and records
+ * HG_ETIMEDOUT in the context's error word (returned by hg_sync); the kernel
+ * then returns normally and the context stays usable.
+ * hg_blockmap_inject_claim is fault injection for tests of that path, made on
+ * the host: it synchronises `stream`, and writes h_digest's tag (host bytes,
+ * dlen long) into its home slot without publishing it, as an insert that
+ * claimed the slot and never finished would leave it. HG_EINVAL if the home
+ * slot is already taken. Clear the map afterwards (hg_blockmap_clear).
+ */
+int hg_blockmap_set_wait_limit(hg_blockmap *map, uint32_t polls);
+int hg_blockmap_inject_claim(hg_blockmap *map, const uint8_t *h_digest, void *stream);
 
 /*
  * Chunk boundaries without allocating: the same result as hg_cdc_boundaries,

@@ -13,7 +13,7 @@ import torch
 
 from . import _lib
 from ._lib import (HG_MD5, HG_SHA1, HashGPUError, check, default_params,  # noqa: F401
-                   hg_batch_autotune, hg_batch_cdc_hash, hg_batch_cdc_hash_graph, hg_batch_create,
+                   hg_batch_autotune, hg_batch_autotune_cached, hg_batch_cdc_hash, hg_batch_cdc_hash_graph, hg_batch_create,
                    hg_batch_destroy, hg_batch_get_tuning, hg_batch_set_tuning, hg_batch_slots,
                    hg_batch_sync, hg_batch_tuning, hg_cdc_boundaries, hg_cdc_boundaries_static,
                    hg_cdc_candidates, hg_cdc_params, hg_destroy, hg_digest_len, hg_hash_blocks,
@@ -24,7 +24,7 @@ from ._lib import (HG_MD5, HG_SHA1, HashGPUError, check, default_params,  # noqa
                    hg_submit, hg_cdc_hash, hg_cdc_hash_plan, hg_cdc_hash_h2d, hg_stream_open,
                    hg_stream_feed, hg_stream_close, hg_stream_destroy, hg_blockmap_create,
                    hg_blockmap_insert, hg_blockmap_lookup, hg_blockmap_count, hg_blockmap_clear,
-                   hg_blockmap_destroy, hg_probe_int_pipe, hg_alloc_pinned, hg_free_pinned,
+                   hg_blockmap_destroy, hg_alloc_pinned, hg_free_pinned,
                    hg_pinned_set_budget, hg_pinned_trim, hg_pinned_stats, hg_pinned_class,
                    hg_pinned_info)
 
@@ -149,10 +149,6 @@ class Context:
         check(hg_hash_blocks(self.h, algo, _ptr(data), n, block, _ptr(out),
                              _ptr(root_out) if root else None, _stream(stream)), "hg_hash_blocks")
         return out, (root_out if root else None)
-
-    def probe_int_pipe(self, kind: int, iters: int, ctas_per_sm: int = 8, stream=None) -> int:
-        """Launch the integer-pipe probe; returns the operations it performs (time it)."""
-        return hg_probe_int_pipe(self.h, kind, iters, ctas_per_sm, _stream(stream))
 
     def hash_blocks_pmd(self, data: torch.Tensor, block: int, segment: int, algo: int = MD5,
                         out: torch.Tensor | None = None, seg_out: torch.Tensor | None = None,
@@ -309,11 +305,23 @@ class Batch:
     def set_tuning(self, t: hg_batch_tuning):
         check(hg_batch_set_tuning(self.h, t), "hg_batch_set_tuning")
 
-    def autotune(self, data: torch.Tensor, algo: int = SHA1, out=None, stream=None) -> hg_batch_tuning:
+    def autotune(self, data: torch.Tensor, algo: int = SHA1, out=None, stream=None,
+                 cache: str | None = None) -> hg_batch_tuning:
+        """Tune this batch (hg_batch_autotune); with `cache` (a JSON Lines file) a tuning
+        stored for the same GPU, parameters and batch shape is reused instead
+        (hg_batch_autotune_cached). `self.tuned_from_cache` tells which happened."""
         ends, counts, dg = out if out is not None else self.outputs(algo)
         best = hg_batch_tuning()
-        check(hg_batch_autotune(self.h, algo, _ptr(data), _ptr(ends), _ptr(counts), _ptr(dg),
-                                _stream(stream), best), "hg_batch_autotune")
+        if cache is None:
+            check(hg_batch_autotune(self.h, algo, _ptr(data), _ptr(ends), _ptr(counts), _ptr(dg),
+                                    _stream(stream), best), "hg_batch_autotune")
+            self.tuned_from_cache = False
+        else:
+            hit = C.c_int(0)
+            check(hg_batch_autotune_cached(self.h, algo, _ptr(data), _ptr(ends), _ptr(counts),
+                                           _ptr(dg), _stream(stream), cache, best, hit),
+                  "hg_batch_autotune_cached")
+            self.tuned_from_cache = bool(hit.value)
         return best
 
     def file_results(self, f: int, ends: torch.Tensor, counts: torch.Tensor, dg: torch.Tensor):

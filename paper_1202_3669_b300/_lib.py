@@ -13,7 +13,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libhashgpu.so")
 
 HG_OK, HG_EINVAL, HG_ENOMEM, HG_ECAPACITY, HG_ETIMEDOUT = 0, -1, -2, -3, -4
-HG_ECUDA, HG_EAGAIN, HG_ECANCELED, HG_EUNSUPPORTED = -5, -6, -7, -8
+HG_ECUDA, HG_EAGAIN, HG_ECANCELED, HG_EUNSUPPORTED, HG_EBOUNDS = -5, -6, -7, -8, -9
 HG_MD5, HG_SHA1 = 0, 1
 
 # every exported symbol the header declares, with (restype, argtypes)
@@ -67,6 +67,7 @@ SIGNATURES = {
     "hg_cdc_default_params": (None, [C.POINTER(hg_cdc_params)]),
     "hg_strerror": (C.c_char_p, [_i32]),
     "hg_digest_len": (_i32, [_i32]),
+    "hg_host_digest": (_i32, [_i32, _vp, _u64, _vp]),
     "hg_init": (_i32, [C.POINTER(_vp), _i32, _sz]),
     "hg_destroy": (_i32, [_vp]),
     "hg_reserve": (_i32, [_vp, _u64]),
@@ -74,13 +75,14 @@ SIGNATURES = {
     "hg_scratch_bytes": (_u64, [_vp]),
     "hg_hash_blocks": (_i32, [_vp, _i32, _vp, _u64, _u64, _vp, _vp, _vp]),
     "hg_hash_blocks_pmd": (_i32, [_vp, _i32, _vp, _u64, _u64, _u64, _vp, _vp, _vp]),
-    "hg_probe_int_pipe": (_i32, [_vp, _i32, _u32, _u32, _vp, _vp]),
     "hg_blockmap_create": (_i32, [_vp, _i32, _u64, _vp]),
     "hg_blockmap_insert": (_i32, [_vp, _vp, _u64, _vp, _vp]),
     "hg_blockmap_lookup": (_i32, [_vp, _vp, _vp, _u64, _vp, _vp, _vp, _vp]),
     "hg_blockmap_count": (_i32, [_vp, _vp, _vp]),
     "hg_blockmap_clear": (_i32, [_vp, _vp]),
     "hg_blockmap_destroy": (_i32, [_vp]),
+    "hg_blockmap_set_wait_limit": (_i32, [_vp, _u32]),
+    "hg_blockmap_inject_claim": (_i32, [_vp, _vp, _vp]),
     "hg_window_bitmap": (_i32, [_vp, _vp, _u64, C.POINTER(hg_cdc_params), _vp, _vp]),
     "hg_cdc_candidates": (_i32, [_vp, _vp, _u64, C.POINTER(hg_cdc_params), _vp, _u64, _vp, _vp]),
     "hg_cdc_boundaries": (_i32, [_vp, _vp, _u64, C.POINTER(hg_cdc_params), _vp, _u64, _vp, _vp]),
@@ -101,6 +103,8 @@ SIGNATURES = {
     "hg_batch_get_tuning": (_i32, [_vp, _vp]),
     "hg_batch_set_tuning": (_i32, [_vp, _vp]),
     "hg_batch_autotune": (_i32, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "hg_batch_autotune_cached": (_i32, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, C.c_char_p, _vp,
+                                        C.POINTER(C.c_int)]),
     "hg_server_default_config": (None, [C.POINTER(hg_server_config)]),
     "hg_server_create": (_i32, [_vp, C.POINTER(hg_server_config), C.POINTER(_vp)]),
     "hg_server_destroy": (_i32, [_vp]),
@@ -275,6 +279,14 @@ def hg_batch_autotune(batch, algo, d_data, d_ends, d_counts, d_digests, stream, 
                                  C.byref(best) if best is not None else None)
 
 
+def hg_batch_autotune_cached(batch, algo, d_data, d_ends, d_counts, d_digests, stream, cache_path,
+                             best, from_cache) -> int:
+    return lib.hg_batch_autotune_cached(batch, algo, d_data, d_ends, d_counts, d_digests, stream,
+                                        cache_path.encode() if isinstance(cache_path, str) else cache_path,
+                                        C.byref(best) if best is not None else None,
+                                        C.byref(from_cache) if from_cache is not None else None)
+
+
 def hg_server_default_config(cfg) -> None:
     lib.hg_server_default_config(C.byref(cfg))
 
@@ -335,12 +347,6 @@ def hg_cdc_hash_plan(n, bounds_ptr, max_n) -> int:
 def hg_cdc_hash_h2d(ctx, algo, h_in, d_in, n, params, d_ends, cap, d_count, d_digests, stream) -> int:
     return lib.hg_cdc_hash_h2d(ctx, algo, h_in, d_in, n, C.byref(params), d_ends, cap, d_count,
                                d_digests, stream)
-
-
-def hg_probe_int_pipe(ctx, kind, iters, ctas_per_sm, stream) -> int:
-    ops = C.c_uint64()
-    check(lib.hg_probe_int_pipe(ctx, kind, iters, ctas_per_sm, C.byref(ops), stream), "hg_probe_int_pipe")
-    return ops.value
 
 
 def hg_blockmap_create(ctx, algo, capacity) -> int:

@@ -11,6 +11,9 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libhashgpu.so")
+# the benchmark's integer-pipe probe: its own library, not part of the hashing library
+PROBE_SRC = os.path.join(PKG, "bench_probe", "hg_probe.cu")
+PROBE_LIB = os.path.join(PKG, "bench_probe", "libhgprobe.so")
 BUILD = os.path.join(PKG, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2,-Wall",
@@ -26,12 +29,19 @@ def headers() -> list[str]:
     return hs + [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
 
 
-def _compile(src: str, verbose: bool) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+# The debug variant (HG_DEBUG): kernels check the indexes of their global accesses
+# and report HG_EBOUNDS instead of touching memory out of range.
+LIB_DEBUG = os.path.join(PKG, "libhashgpu_debug.so")
+BUILD_DEBUG = os.path.join(PKG, "_build_debug")
+
+
+def _compile(src: str, verbose: bool, debug: bool = False) -> str:
+    obj = os.path.join(BUILD_DEBUG if debug else BUILD, os.path.basename(src) + ".o")
     newest = max(os.path.getmtime(p) for p in [src, *headers(), __file__])
     if os.path.exists(obj) and os.path.getmtime(obj) >= newest:
         return obj
-    cmd = ["nvcc", *NVCC_FLAGS, *(["-Xptxas", "-v"] if verbose else []), "-c", src, "-o", obj]
+    cmd = ["nvcc", *NVCC_FLAGS, *(["-DHG_DEBUG"] if debug else []),
+           *(["-Xptxas", "-v"] if verbose else []), "-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -40,20 +50,35 @@ def _compile(src: str, verbose: bool) -> str:
     return obj
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    bdir, lib = (BUILD_DEBUG, LIB_DEBUG) if debug else (BUILD, LIB)
+    os.makedirs(bdir, exist_ok=True)
     if force:
-        for f in os.listdir(BUILD):
-            os.remove(os.path.join(BUILD, f))
+        for f in os.listdir(bdir):
+            os.remove(os.path.join(bdir, f))
     with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose), sources()))
-    if not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
-        tmp = LIB + ".tmp"
+        objs = list(ex.map(lambda s: _compile(s, verbose, debug), sources()))
+    if not os.path.exists(lib) or any(os.path.getmtime(o) > os.path.getmtime(lib) for o in objs):
+        tmp = lib + ".tmp"
         cmd = ["nvcc", "-shared", *ARCH, "-o", tmp, *objs, "-cudart", "static"]
         subprocess.run(cmd, check=True)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
+
+
+def build_probe(force: bool = False) -> str:
+    """Build the benchmark's probe library (libhgprobe.so) beside its source."""
+    if force or not os.path.exists(PROBE_LIB) or os.path.getmtime(PROBE_LIB) < max(
+            os.path.getmtime(PROBE_SRC), os.path.getmtime(__file__)):
+        tmp = PROBE_LIB + ".tmp"
+        cmd = ["nvcc", "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", *ARCH, "-shared",
+               PROBE_SRC, "-o", tmp, "-cudart", "static"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, PROBE_LIB)
+    return PROBE_LIB
 
 
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, debug=True))
+    print(build_probe(force="--force" in sys.argv))

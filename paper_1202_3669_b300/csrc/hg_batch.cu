@@ -6,6 +6,9 @@
 #include <new>
 #include <vector>
 
+#include <cstdio>
+#include <string>
+
 #include "hg_internal.h"
 
 using namespace hg;
@@ -254,6 +257,82 @@ int hg_batch_autotune(hg_batch *b, int algo, const uint8_t *d_data, uint64_t *d_
     cudaEventDestroy(e1);
     if (best) *best = top;
     return rc;
+}
+
+}  // extern "C"
+
+// Autotuner cache (JSON Lines): one line per tuned configuration,
+//   {"key": {...}, "tuning": {...}}
+// keyed by the GPU (name, SM count), the algorithm, the chunking parameters and
+// the batch's shape (file count, log2 of its bytes, files of 1 MiB and up).
+static std::string tune_key(const hg_batch *b, int algo) {
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, b->ctx->device);
+    const uint32_t big = (uint32_t)b->host.big.size();     // files selected by a whole CTA
+    int lg = 0;
+    while ((2ull << lg) <= b->total) lg++;
+    char buf[512];
+    std::snprintf(buf, sizeof buf,
+                  "{\"gpu\": \"%s\", \"sms\": %d, \"algo\": %d, \"window\": %u, \"mask_bits\": %u, "
+                  "\"magic\": %u, \"window_hash\": %u, \"min_chunk\": %llu, \"max_chunk\": %llu, "
+                  "\"nfile\": %u, \"bytes_log2\": %d, \"big_files\": %u}",
+                  prop.name, prop.multiProcessorCount, algo, b->p.window, b->p.mask_bits, b->p.magic,
+                  b->p.window_hash, (unsigned long long)b->p.min_chunk,
+                  (unsigned long long)b->p.max_chunk, b->nfile, lg, big);
+    return buf;
+}
+
+static bool tune_lookup(const char *path, const std::string &key, hg_batch_tuning *t) {
+    FILE *f = std::fopen(path, "r");
+    if (!f) return false;
+    char line[2048];
+    const std::string want = "{\"key\": " + key + ", \"tuning\": ";
+    bool found = false;
+    while (std::fgets(line, sizeof line, f)) {
+        if (std::strncmp(line, want.c_str(), want.size()) != 0) continue;
+        int w = 0, ht = 0, hc = 0;
+        unsigned long long lb = 0;
+        if (std::sscanf(line + want.size(),
+                        "{\"window_ctas_per_sm\": %d, \"hash_threads\": %d, \"hash_ctas_per_sm\": %d, "
+                        "\"long_chunk_bytes\": %llu}",
+                        &w, &ht, &hc, &lb) == 4 &&
+            w >= 1 && ht >= 32 && ht <= 512 && hc >= 1) {
+            *t = hg_batch_tuning{w, ht, hc, 0, lb};
+            found = true;               // the last matching line wins
+        }
+    }
+    std::fclose(f);
+    return found;
+}
+
+extern "C" {
+
+int hg_batch_autotune_cached(hg_batch *b, int algo, const uint8_t *d_data, uint64_t *d_ends,
+                             uint64_t *d_counts, uint8_t *d_digests, void *stream,
+                             const char *cache_path, hg_batch_tuning *best, int *from_cache) {
+    if (!b || !cache_path) return HG_EINVAL;
+    if (from_cache) *from_cache = 0;
+    const std::string key = tune_key(b, algo);
+    hg_batch_tuning t{};
+    if (tune_lookup(cache_path, key, &t)) {
+        const int r = hg_batch_set_tuning(b, &t);
+        if (r) return r;
+        if (best) *best = t;
+        if (from_cache) *from_cache = 1;
+        return HG_OK;
+    }
+    const int r = hg_batch_autotune(b, algo, d_data, d_ends, d_counts, d_digests, stream, &t);
+    if (r) return r;
+    if (best) *best = t;
+    FILE *f = std::fopen(cache_path, "a");
+    if (!f) return HG_OK;               // tuned; the cache is only an optimisation
+    std::fprintf(f,
+                 "{\"key\": %s, \"tuning\": {\"window_ctas_per_sm\": %d, \"hash_threads\": %d, "
+                 "\"hash_ctas_per_sm\": %d, \"long_chunk_bytes\": %llu}}\n",
+                 key.c_str(), t.window_ctas_per_sm, t.hash_threads, t.hash_ctas_per_sm,
+                 (unsigned long long)t.long_chunk_bytes);
+    std::fclose(f);
+    return HG_OK;
 }
 
 }  // extern "C"

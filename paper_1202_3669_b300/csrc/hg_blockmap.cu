@@ -20,6 +20,7 @@
 // completes within a few instructions; the wait is bounded and reports
 // HG_ETIMEDOUT through the context's error word if it ever runs out).
 // Lookups run in a later launch, when every claimed slot is published.
+#include <cstring>
 #include <new>
 
 #include "hg_internal.h"
@@ -33,6 +34,7 @@ struct hg_blockmap {
     unsigned long long *entries = nullptr;     // distinct digests stored
     void *mem = nullptr;
     size_t mem_bytes = 0;
+    uint32_t wait_limit = 0;                    // polls of a claimed slot's publish word
 };
 
 namespace hg {
@@ -68,9 +70,10 @@ __device__ __forceinline__ uint32_t ld_ready(const uint4 *p) {
     return v;
 }
 
-// Waits (bounded) until slot s is published; false if the wait ran out.
-__device__ __forceinline__ bool wait_ready(const uint4 *rest, uint64_t s) {
-    for (uint32_t i = 0; i < kReadyWaitLimit; i++)
+// Waits (bounded: `limit` polls) until slot s is published; false if the wait
+// ran out.
+__device__ __forceinline__ bool wait_ready(const uint4 *rest, uint64_t s, uint32_t limit) {
+    for (uint32_t i = 0; i < limit; i++)
         if (ld_ready(rest + s)) return true;
     return false;
 }
@@ -84,7 +87,8 @@ __global__ void __launch_bounds__(kBmThreads) k_bm_insert(const uint8_t *__restr
                                                           uint64_t count, const uint64_t *d_count,
                                                           unsigned long long *tags, uint4 *rest,
                                                           uint64_t mask,
-                                                          unsigned long long *entries, int *err) {
+                                                          unsigned long long *entries, int *err,
+                                                          uint32_t wait_limit) {
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     uint64_t cnt = count;
     if (d_count) cnt = min(cnt, *d_count);
@@ -106,7 +110,7 @@ __global__ void __launch_bounds__(kBmThreads) k_bm_insert(const uint8_t *__restr
             }
         }
         if (t == k.tag) {
-            if (!wait_ready(rest, s)) {
+            if (!wait_ready(rest, s, wait_limit)) {
                 atomicCAS(err, 0, (int)HG_ETIMEDOUT);
                 return;
             }
@@ -203,6 +207,7 @@ int hg_blockmap_create(hg_ctx *ctx, int algo, uint64_t capacity, hg_blockmap **o
     m->tags = reinterpret_cast<unsigned long long *>(b + nslots * sizeof(uint4));
     m->entries = reinterpret_cast<unsigned long long *>(b + nslots * (sizeof(uint4) + 8));
     m->mem_bytes = bytes;
+    m->wait_limit = kReadyWaitLimit;
     ctx->held += bytes;
     *out = m;
     return HG_OK;
@@ -218,7 +223,7 @@ int hg_blockmap_insert(hg_blockmap *m, const uint8_t *d_digests, uint64_t count,
     const unsigned grid = (unsigned)((count + kBmThreads - 1) / kBmThreads);
     k_bm_insert<<<grid, kBmThreads, 0, (cudaStream_t)stream>>>(
         d_digests, hg_digest_len(m->algo), count, d_count, m->tags, m->rest, m->nslots - 1,
-        m->entries, m->ctx->d_err);
+        m->entries, m->ctx->d_err, m->wait_limit);
     const int r = cuda_status(cudaGetLastError());
     cudaSetDevice(prev);
     return r;
@@ -265,6 +270,35 @@ int hg_blockmap_clear(hg_blockmap *m, void *stream) {
     cudaGetDevice(&prev);
     cudaSetDevice(m->ctx->device);
     const int r = cuda_status(cudaMemsetAsync(m->mem, 0, m->mem_bytes, (cudaStream_t)stream));
+    cudaSetDevice(prev);
+    return r;
+}
+
+int hg_blockmap_set_wait_limit(hg_blockmap *m, uint32_t polls) {
+    if (!m) return HG_EINVAL;
+    m->wait_limit = polls ? polls : kReadyWaitLimit;
+    return HG_OK;
+}
+
+int hg_blockmap_inject_claim(hg_blockmap *m, const uint8_t *h_digest, void *stream) {
+    if (!m || !h_digest) return HG_EINVAL;
+    // the tag and home slot of the digest, as the kernels form them
+    uint32_t w[4];
+    std::memcpy(w, h_digest, sizeof w);
+    unsigned long long tag = (unsigned long long)w[0] | ((unsigned long long)w[1] << 32);
+    if (tag == 0) tag = 1;
+    const uint64_t s = ((uint64_t)w[2] | ((uint64_t)w[3] << 32)) & (m->nslots - 1);
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(m->ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned long long cur = 1;
+    int r = cuda_status(cudaStreamSynchronize(st));
+    if (r == HG_OK)
+        r = cuda_status(cudaMemcpy(&cur, m->tags + s, sizeof cur, cudaMemcpyDeviceToHost));
+    if (r == HG_OK && cur != 0) r = HG_EINVAL;              // the home slot is taken
+    if (r == HG_OK)
+        r = cuda_status(cudaMemcpy(m->tags + s, &tag, sizeof tag, cudaMemcpyHostToDevice));
     cudaSetDevice(prev);
     return r;
 }

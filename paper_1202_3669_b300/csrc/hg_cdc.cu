@@ -118,7 +118,8 @@ __global__ void __launch_bounds__(kWinThreads) k_compact(const uint32_t *__restr
     while (w) {
         const int b = __ffs(w) - 1;
         w &= w - 1;
-        if (idx < cap) cands[idx] = pos0 + b + 1;      // cut after the window's last byte
+        if (idx < cap && HG_DOK(pos0 + b < nwords * 32, nullptr))
+            cands[idx] = pos0 + b + 1;                  // cut after the window's last byte
         idx++;
     }
 }
@@ -284,7 +285,8 @@ __global__ void __launch_bounds__(128) k_hash_seg(const uint8_t *__restrict__ in
                                                   const uint64_t *__restrict__ ends,
                                                   const PipeState *st, int seg,
                                                   const uint32_t *__restrict__ long_idx,
-                                                  uint32_t klong, uint8_t *__restrict__ out) {
+                                                  uint32_t klong, uint8_t *__restrict__ out,
+                                                  uint64_t n, int *err) {
     const uint64_t lo = st->seg_cnt[seg], hi = st->seg_cnt[seg + 1];
     const uint32_t long_ctas = (klong + 3) / 4;
     uint64_t i;
@@ -299,6 +301,7 @@ __global__ void __launch_bounds__(128) k_hash_seg(const uint8_t *__restrict__ in
         if (ends[i] - a0 >= st->thr[seg]) return;          // on a lone lane
     }
     const uint64_t a = i ? ends[i - 1] : st->start0, b = ends[i];
+    if (!HG_DOK(a <= b && b <= n, err)) return;
     H hs;
     hash_range(in + a, b - a, hs);
     store_digest(hs, out + i * H::kDigest);
@@ -366,7 +369,8 @@ __global__ void __launch_bounds__(128) k_hash_sorted(const uint8_t *__restrict__
                                                      const uint64_t *__restrict__ ends,
                                                      PipeState *st,
                                                      const uint32_t *__restrict__ tasks,
-                                                     uint32_t klong, uint8_t *__restrict__ out) {
+                                                     uint32_t klong, uint8_t *__restrict__ out,
+                                                     uint64_t n, int *err) {
     const uint64_t cnt = st->count, s0 = st->start0;
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t long_ctas = (klong + 3) / 4;
@@ -375,6 +379,7 @@ __global__ void __launch_bounds__(128) k_hash_sorted(const uint8_t *__restrict__
         if (lane || k >= klong || k >= cnt) return;
         const uint64_t i = tasks[k];
         const uint64_t a = i ? ends[i - 1] : s0;
+        if (!HG_DOK(i < cnt && a <= ends[i] && ends[i] <= n, err)) return;
         H hs;
         hash_range(in + a, ends[i] - a, hs);
         store_digest(hs, out + i * H::kDigest);
@@ -389,9 +394,11 @@ __global__ void __launch_bounds__(128) k_hash_sorted(const uint8_t *__restrict__
         if (k < cnt) {
             const uint64_t i = tasks[k];
             const uint64_t a = i ? ends[i - 1] : s0;
-            H hs;
-            hash_range(in + a, ends[i] - a, hs);
-            store_digest(hs, out + i * H::kDigest);
+            if (HG_DOK(i < cnt && a <= ends[i] && ends[i] <= n, err)) {
+                H hs;
+                hash_range(in + a, ends[i] - a, hs);
+                store_digest(hs, out + i * H::kDigest);
+            }
         }
     }
 }
@@ -506,17 +513,17 @@ int launch_pipe_segment(const uint8_t *d_in, uint64_t n, uint64_t n_sel, const h
     const unsigned grid = (unsigned)((max_chunks + 127) / 128 + (b.klong + 3) / 4);
     if (algo == HG_MD5)
         k_hash_seg<Md5Chain><<<grid, 128, 0, s_hash>>>(d_in, b.ends, b.st, seg, b.long_idx, b.klong,
-                                                       b.digests);
+                                                       b.digests, n, b.err);
     else
         k_hash_seg<Sha1><<<grid, 128, 0, s_hash>>>(d_in, b.ends, b.st, seg, b.long_idx, b.klong,
-                                                   b.digests);
+                                                   b.digests, n, b.err);
     return cuda_status(cudaGetLastError());
 }
 
 constexpr uint64_t kBulkCtasPerSm = 1;
 
-int launch_hash_sorted(const uint8_t *d_in, uint64_t max_chunks, const hg_cdc_params &p, int algo,
-                       const PipeBufs &b, cudaStream_t s) {
+int launch_hash_sorted(const uint8_t *d_in, uint64_t n, uint64_t max_chunks, const hg_cdc_params &p,
+                       int algo, const PipeBufs &b, cudaStream_t s) {
     const unsigned sgrid = 4 * 148;
     k_len_hist<<<sgrid, 256, 0, s>>>(b.ends, b.st, p.max_chunk);
     k_len_scan<<<1, 32, 0, s>>>(b.st);
@@ -526,9 +533,11 @@ int launch_hash_sorted(const uint8_t *d_in, uint64_t max_chunks, const hg_cdc_pa
     const uint64_t need = ((max_chunks + 31) / 32 + 3) / 4;
     const unsigned grid = (unsigned)((b.klong + 3) / 4 + (need < bulk_ctas ? need : bulk_ctas));
     if (algo == HG_MD5)
-        k_hash_sorted<Md5Chain><<<grid, 128, 0, s>>>(d_in, b.ends, b.st, b.tasks, b.klong, b.digests);
+        k_hash_sorted<Md5Chain><<<grid, 128, 0, s>>>(d_in, b.ends, b.st, b.tasks, b.klong, b.digests,
+                                                     n, b.err);
     else
-        k_hash_sorted<Sha1><<<grid, 128, 0, s>>>(d_in, b.ends, b.st, b.tasks, b.klong, b.digests);
+        k_hash_sorted<Sha1><<<grid, 128, 0, s>>>(d_in, b.ends, b.st, b.tasks, b.klong, b.digests, n,
+                                                 b.err);
     return cuda_status(cudaGetLastError());
 }
 

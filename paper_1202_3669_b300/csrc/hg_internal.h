@@ -2,6 +2,7 @@
 #pragma once
 #include <cstddef>
 #include <cstdint>
+#include <deque>
 #include <mutex>
 #include <vector>
 #include <cuda_runtime.h>
@@ -10,6 +11,10 @@
 
 namespace hg {
 struct PinnedPool;
+struct RootJob {          // a hash-of-hashes computed on the host (hg_hostroot.cu)
+    int algo;
+    uint64_t nbytes;
+};
 }
 
 struct hg_ctx {
@@ -41,6 +46,12 @@ struct hg_ctx {
     // pinned host buffer pool (hg_pinned.cu), created on first use
     std::mutex pinned_mu;
     struct hg::PinnedPool *pinned = nullptr;
+    // host-side hash-of-hashes: pinned staging (digests, then a 64-byte root
+    // slot at root_cap) and the jobs enqueued but not yet run, in stream order
+    uint8_t *root_stage = nullptr;
+    uint64_t root_cap = 0;
+    std::mutex root_mu;
+    std::deque<hg::RootJob> root_jobs;
 };
 
 namespace hg {
@@ -146,8 +157,8 @@ int launch_window_rabin_range(const uint8_t *d_in, uint64_t n, const hg_cdc_para
 // on lone lanes, the rest 32 to a warp in that order. Used when a buffer has
 // several segments, where per-segment digest launches would share the SMs
 // with the later segments' window kernels.
-int launch_hash_sorted(const uint8_t *d_in, uint64_t max_chunks, const hg_cdc_params &p, int algo,
-                       const PipeBufs &b, cudaStream_t s);
+int launch_hash_sorted(const uint8_t *d_in, uint64_t n, uint64_t max_chunks, const hg_cdc_params &p,
+                       int algo, const PipeBufs &b, cudaStream_t s);
 // digests = false: the segment's digests are left to launch_hash_sorted.
 int launch_pipe_segment(const uint8_t *d_in, uint64_t n, uint64_t n_sel, const hg_cdc_params &p,
                         int algo, uint32_t tile0, uint32_t ntiles, uint64_t L, int seg,
@@ -167,6 +178,33 @@ int launch_select(const uint64_t *d_cands, const uint64_t *d_ncand, uint64_t can
                   uint64_t cap, uint64_t *d_count, cudaStream_t s);
 
 inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? HG_OK : HG_ECUDA; }
+
+// Debug build (HG_DEBUG, libhashgpu_debug.so): kernels check the index of a
+// global access that is not in range by construction alone; a failed check
+// records HG_EBOUNDS in the error word and the access is skipped. In the
+// release build HG_DOK is `true` and costs nothing.
+#ifdef HG_DEBUG
+#ifdef __CUDACC__
+__device__ __forceinline__ bool hg_dok(bool ok, int *err) {
+    if (!ok && err) atomicCAS(err, 0, (int)HG_EBOUNDS);
+    return ok;
+}
+#endif
+#define HG_DOK(cond, err) (::hg::hg_dok((cond), (err)))
+#else
+#define HG_DOK(cond, err) true
+#endif
+
+// hg_hostroot.cu: the library's host MD5/SHA-1, and the hash-of-hashes
+// computed on a host core in stream order (digests copied to pinned staging,
+// hashed by a host function, the root copied back). Digest lists shorter than
+// kHostRootMinBytes, and calls on a capturing stream, use the device chain.
+// HG_HOST_ROOT_MIN (bytes, read once) overrides the threshold.
+constexpr uint64_t kHostRootMinBytes = 8192;
+uint64_t host_root_min_bytes();
+void host_digest(int algo, const uint8_t *msg, uint64_t n, uint8_t *out);
+int enqueue_host_root(hg_ctx *c, int algo, const uint8_t *d_digests, uint64_t nbytes, uint8_t *d_root,
+                      cudaStream_t s);
 
 // hg_pinned.cu: the pinned host buffer pool.
 constexpr uint64_t kPinnedDefaultBudget = 16ull << 30;

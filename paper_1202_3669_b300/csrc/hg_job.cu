@@ -299,7 +299,7 @@ __global__ void k_job_tasks(JobDev j, const uint64_t *__restrict__ ends,
 template <class H>
 __global__ void k_job_hash(JobDev j, const uint64_t *__restrict__ ends,
                            const uint64_t *__restrict__ tasks, unsigned long long *words,
-                           uint8_t *__restrict__ digests) {
+                           uint8_t *__restrict__ digests, int *err) {
     const int lane = threadIdx.x & 31;
     const uint64_t total = words[kJobTotal];
     while (true) {
@@ -311,8 +311,11 @@ __global__ void k_job_hash(JobDev j, const uint64_t *__restrict__ ends,
         if (k < total) {
             const uint64_t tk = tasks[k];
             const uint32_t f = (uint32_t)(tk >> 32), i = (uint32_t)tk;
+            if (!HG_DOK(f < j.nfile, err)) continue;
             const uint64_t so = j.slot_off[f];
+            if (!HG_DOK(so + i < j.slot_off[f + 1], err)) continue;
             const uint64_t lo = i ? ends[so + i - 1] : 0, hi = ends[so + i];
+            if (!HG_DOK(lo <= hi && hi <= jlen(j, f), err)) continue;
             H hs;
             hash_range(jptr(j, f) + lo, hi - lo, hs);
             store_digest(hs, digests + (so + i) * H::kDigest);
@@ -508,9 +511,11 @@ int enqueue_cdc_job(const JobDev &j, const JobScratch &sc, const hg_cdc_params &
     }
     const int hgrid = num_sms * tn.hash_ctas;
     if (algo == HG_MD5)
-        k_job_hash<Md5Chain><<<hgrid, tn.hash_threads, 0, s>>>(j, d_ends, sc.tasks, sc.words, d_digests);
+        k_job_hash<Md5Chain><<<hgrid, tn.hash_threads, 0, s>>>(j, d_ends, sc.tasks, sc.words, d_digests,
+                                                                sc.err);
     else
-        k_job_hash<Sha1><<<hgrid, tn.hash_threads, 0, s>>>(j, d_ends, sc.tasks, sc.words, d_digests);
+        k_job_hash<Sha1><<<hgrid, tn.hash_threads, 0, s>>>(j, d_ends, sc.tasks, sc.words, d_digests,
+                                                            sc.err);
     return cuda_status(cudaGetLastError());
 }
 

@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(kWinThreads) k_window_bitmap(const uint8_t *__
         uint32_t s = 0;
 #pragma unroll
         for (int w = 0; w < kWinThreads / 32; w++) s += warp_cnt[w];
-        tile_cnt[tix] = s;
+        if (HG_DOK((uint64_t)tix * kWinTile < n, err)) tile_cnt[tix] = s;
     }
 }
 

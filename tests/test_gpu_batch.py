@@ -120,3 +120,40 @@ def test_config_batch_4096_files(hg):
     counts = out[1].cpu().numpy()
     assert (counts >= np.ceil(sizes / 65536)).all()
     assert (counts <= sizes // 2048 + 1).all()
+
+
+def test_autotune_cache_reuses_tuning(hg, tmp_path):
+    """The autotuner cache: the first call tunes and appends a line keyed by GPU,
+    parameters and batch shape; the second finds it and tunes nothing; another batch
+    shape misses."""
+    import json
+
+    import paper_1202_3669_b300 as hgb
+    sizes = G.lognormal_sizes(150, seed=71, median=48 * 1024, sigma=1.3, hi=4 << 20)
+    data, off = G.files_from_sizes(sizes, 72)
+    d = to_device(data)
+    cache = str(tmp_path / "autotune.jsonl")
+    b = hgb.Batch(hg, off)
+    t1 = b.autotune(d, hgb.SHA1, cache=cache)
+    assert not b.tuned_from_cache
+    t2 = b.autotune(d, hgb.SHA1, cache=cache)
+    assert b.tuned_from_cache
+    assert (t1.window_ctas_per_sm, t1.hash_threads, t1.hash_ctas_per_sm) == \
+        (t2.window_ctas_per_sm, t2.hash_threads, t2.hash_ctas_per_sm)
+    lines = open(cache).read().splitlines()
+    assert len(lines) == 1
+    rec = json.loads(lines[0])
+    assert rec["key"]["nfile"] == 150 and rec["key"]["algo"] == hgb.SHA1
+    assert rec["tuning"]["hash_threads"] == t1.hash_threads
+    out = b.cdc_hash(d, hgb.SHA1)                # results with the cached tuning
+    b.sync()
+    b.close()
+    b2 = hgb.Batch(hg, off[:101])                # another shape: a miss, a second line
+    b2.autotune(d, hgb.MD5, cache=cache)
+    assert not b2.tuned_from_cache and len(open(cache).read().splitlines()) == 2
+    b2.close()
+    want = oracle_files(data, off, hgb.default_params(), oracle.SHA1)
+    so = np.asarray(hgb.Batch(hg, off).slot_off, dtype=np.int64)
+    for f in (0, 50, 149):
+        k = int(out[1][f].item())
+        assert np.array_equal(out[0][so[f]:so[f] + k].cpu().numpy().astype(np.uint64), want[f][0])

@@ -145,13 +145,19 @@ def test_two_level_bad_arguments(hg):
     hg.sync()
 
 
-def test_int_pipe_probe_runs(hg):
-    """The integer-pipe probe (roofline denominator) launches and reports its op count."""
-    import paper_1202_3669_b300 as hgb
+def test_int_pipe_probe_runs():
+    """The benchmark's integer-pipe probe (roofline denominators, its own library)
+    launches and reports its operation count; bad arguments are refused."""
+    import ctypes as C
+    import os
+    lib = C.CDLL(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                              "paper_1202_3669_b300", "bench_probe", "libhgprobe.so"))
+    lib.hgp_probe_int_pipe.argtypes = [C.c_int, C.c_int, C.c_uint32, C.c_uint32, C.c_void_p, C.c_void_p]
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    for kind in range(4):
-        ops = hg.probe_int_pipe(kind, 64, 2)
-        assert ops == sms * 2 * 256 * 8 * 64 * (4 if kind == 3 else 1)
-    with pytest.raises(hgb.HashGPUError):
-        hg.probe_int_pipe(4, 64, 2)
-    hg.sync()
+    ops = C.c_uint64()
+    s = torch.cuda.current_stream().cuda_stream
+    for kind in range(5):
+        assert lib.hgp_probe_int_pipe(0, kind, 64, 2, C.byref(ops), s) == 0
+        assert ops.value == sms * 2 * 256 * 8 * 64 * (4 if kind == 3 else 1)
+    assert lib.hgp_probe_int_pipe(0, 5, 64, 2, C.byref(ops), s) != 0
+    torch.cuda.synchronize()

@@ -48,10 +48,12 @@ def test_host_budget():
     d = ctx.alloc_pinned(2 << 20)                    # 9 MiB would not fit: the free 5 MiB goes
     st = ctx.pinned_stats()
     assert st["held_bytes"] == 4 << 20 and st["in_use_bytes"] == 4 << 20 and st["buffers"] == 2
+    from paper_1202_3669_b300 import _lib
+    pb = b.ptr
     b.free()
     d.free()
-    with pytest.raises(hgb.HashGPUError):
-        b.free()                                     # already given back
+    assert _lib.lib.hg_free_pinned(ctx.h, pb) == _lib.HG_EINVAL      # already given back
+    assert _lib.lib.hg_free_pinned(ctx.h, pb + 64) == _lib.HG_EINVAL  # not a pool buffer
     ctx.close()
 
 
