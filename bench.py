@@ -76,7 +76,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the direct/batch/serve/CPU legs")
     ap.add_argument("--leg", default=None,
-                    choices=["direct", "batch", "serve", "rabin", "blockmap", "configs", "alu"],
+                    choices=["direct", "batch", "serve", "rabin", "blockmap", "configs", "alu", "blocks"],
                     help="run only this extra leg (for profiling) and print its result")
     ap.add_argument("--batch-files", type=int, default=4096,
                     help="batch leg: use only the first N files of the 4096-file workload")
@@ -375,6 +375,8 @@ def main():
             res = configs_leg(hgb, ctx, dev, flush)
         elif args.leg == "alu":
             res = alu_leg(dev)
+        elif args.leg == "blocks":
+            res = blocks_leg(hgb, ctx, dev)
         else:
             bl = batch_leg(hgb, ctx, dev, flush)
             res = serve_leg(hgb, ctx, bl["batched_graph_GBps"], bl["per_file_GBps"])
@@ -690,6 +692,29 @@ def direct_leg(hgb, ctx, dev, flush):
     ctx.sync()
     res["note"] = (f"1 GiB uniform bytes (seed 4); 262144 / 16384 / 1024 blocks; two-level = "
                    f"H(4 KiB segment digests) per 1 MiB block; HBM peak {peaks['hbm_gbs']} GB/s ({kind})")
+    return res
+
+
+def blocks_leg(hgb, ctx, dev, reps=3):
+    """Fixed-block digests of 1 GiB of uniform bytes in 4 KiB blocks, reps launches of MD5
+    then reps of SHA-1, without the root (a short, fixed launch sequence for profiling)."""
+    import torch
+    from gen import inputs as G
+    data = torch.from_numpy(G.uniform_bytes(1 << 30, seed=4)).to(dev)
+    s = torch.cuda.current_stream(dev)
+    res = {}
+    for algo, name, dl in ((hgb.MD5, "md5", 16), (hgb.SHA1, "sha1", 20)):
+        out = torch.empty(((1 << 30) // 4096, dl), dtype=torch.uint8, device=dev)
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            ctx.hash_blocks(data, 4096, algo, root=False, out=out)
+            b.record(s)
+            ts.append((a, b))
+        torch.cuda.synchronize()
+        res[name] = {"ms": [x.elapsed_time(y) for x, y in ts]}
+    ctx.sync()
     return res
 
 

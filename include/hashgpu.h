@@ -181,8 +181,10 @@ uint64_t hg_pinned_class(uint64_t bytes);
  * copied to a pinned staging buffer of the context, hashed by a host function
  * enqueued on `stream`, and the root is copied back, all in stream order
  * (the staging buffer grows on demand, which synchronises the device once).
- * Digest lists under 8 KiB, and calls made while `stream` is being captured
- * into a CUDA graph, use a single-thread device kernel instead.
+ * Shorter digest lists (MD5: under 1 MiB; SHA-1: under 16 KiB when the host
+ * CPU has the SHA extensions, else under 256 KiB; the environment variable
+ * HG_HOST_ROOT_MIN, in bytes, overrides both), and calls made while `stream`
+ * is being captured into a CUDA graph, use a single-thread device kernel.
  * d_in: n bytes, any alignment. d_digests: nblk*dlen bytes, 4-byte aligned.
  * d_root: dlen bytes or NULL. Errors: HG_EINVAL (block == 0, bad algo,
  * null or misaligned buffer).

@@ -65,9 +65,10 @@ def _stream(stream) -> int:
 class PinnedBuffer:
     """A page-locked host buffer from a context's pool (hg_alloc_pinned).
 
-    `tensor` is a uint8 CPU tensor of the requested length over the buffer (torch
-    sees it as pinned, so copies from it are asynchronous); it must not be used
-    after `free()`, which gives the buffer back to the pool for reuse.
+    `tensor` is a uint8 CPU tensor of the requested length over the buffer. The
+    driver treats the memory as page-locked (copies from and to it are one DMA and
+    asynchronous), although torch's `is_pinned()` only knows its own allocator. It
+    must not be used after `free()`, which gives the buffer back to the pool.
     """
 
     def __init__(self, ctx: "Context", nbytes: int):

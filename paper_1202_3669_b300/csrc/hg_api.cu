@@ -213,7 +213,7 @@ int hg_hash_blocks(hg_ctx *c, int algo, const uint8_t *d_in, uint64_t n, uint64_
         cudaGetLastError();
         cs = cudaStreamCaptureStatusActive;
     }
-    if (nbytes >= host_root_min_bytes() && cs == cudaStreamCaptureStatusNone)
+    if (nbytes >= host_root_min_bytes(algo) && cs == cudaStreamCaptureStatusNone)
         return enqueue_host_root(c, algo, d_digests, nbytes, d_root, s);
     return launch_root(algo, d_digests, nbytes, d_root, s);
 }

@@ -26,20 +26,42 @@ __global__ void __launch_bounds__(128) k_hash_blocks(const uint8_t *__restrict__
 // One full block of a 16-byte aligned input whose block size is a multiple of
 // 64: four aligned 16-byte loads per MD5/SHA-1 block and the padding block as
 // constants.
-template <class H>
+// 32 bytes of global memory into eight registers (one 256-bit load; the
+// address must be 32-byte aligned).
+__device__ __forceinline__ void ld32(const uint8_t *p, uint32_t *v) {
+    asm volatile("ld.global.nc.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                   "=r"(v[6]), "=r"(v[7])
+                 : "l"(p));
+}
+
+// LOAD32: two 32-byte loads per 64-byte block (the input is 32-byte aligned):
+// a thread's loads touch one 128-byte line each, so a warp load costs 32 L1
+// wavefronts for 1 KiB instead of 512 bytes (the 16-byte form is bound by L1
+// tag throughput on MD5).
+template <class H, bool LOAD32>
 __device__ __forceinline__ void hash_aligned_block(const uint8_t *__restrict__ in, uint64_t block,
                                                    uint64_t i, uint8_t *__restrict__ out,
                                                    uint32_t one) {
-    const uint4 *p = reinterpret_cast<const uint4 *>(in + i * block);
+    const uint8_t *base = in + i * block;
+    const uint4 *p = reinterpret_cast<const uint4 *>(base);
     const uint64_t nb = block >> 6;
     H hs;
     hs.init();
     hs.set_one(one);
     for (uint64_t k = 0; k < nb; k++) {
-        const uint4 x0 = __ldg(p + 4 * k), x1 = __ldg(p + 4 * k + 1);
-        const uint4 x2 = __ldg(p + 4 * k + 2), x3 = __ldg(p + 4 * k + 3);
-        const uint32_t M[16] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w,
-                                x2.x, x2.y, x2.z, x2.w, x3.x, x3.y, x3.z, x3.w};
+        uint32_t M[16];
+        if constexpr (LOAD32) {
+            ld32(base + 64 * k, M);
+            ld32(base + 64 * k + 32, M + 8);
+        } else {
+            const uint4 x0 = __ldg(p + 4 * k), x1 = __ldg(p + 4 * k + 1);
+            const uint4 x2 = __ldg(p + 4 * k + 2), x3 = __ldg(p + 4 * k + 3);
+            M[0] = x0.x; M[1] = x0.y; M[2] = x0.z; M[3] = x0.w;
+            M[4] = x1.x; M[5] = x1.y; M[6] = x1.z; M[7] = x1.w;
+            M[8] = x2.x; M[9] = x2.y; M[10] = x2.z; M[11] = x2.w;
+            M[12] = x3.x; M[13] = x3.y; M[14] = x3.z; M[15] = x3.w;
+        }
         hs.compress(M);
     }
     uint32_t Z[16] = {0x80u, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
@@ -50,22 +72,28 @@ __device__ __forceinline__ void hash_aligned_block(const uint8_t *__restrict__ i
 
 // Many blocks: the throughput form. MD5 is capped at 32 registers so 2048
 // threads fit an SM: with one chain per thread, occupancy is what hides the
-// loads (measured 4.1 vs 3.3 TB/s for the same loop at 37 registers). SHA-1
-// runs Sha1Split with pipe policy 3 (e + W on the FMA pipe) at 12 CTAs per SM
-// (40 registers, no spills): 1 GiB in 4 KiB blocks 0.534 -> 0.461 ms; at 16
-// CTAs per SM the same code spills.
-template <class H> struct AlignedForm { using Hash = H; static constexpr int kMinCtas = 16; };
+// loads (measured 4.1 vs 3.3 TB/s for the same loop at 37 registers); it runs
+// Md5Split with pipe policy 1 (the logic op's add on the FMA pipe) and, on a
+// 32-byte aligned input, 32-byte loads: 1 GiB in 4 KiB blocks 0.248 -> 0.239 ms.
+// SHA-1 runs Sha1Split with pipe policy 3 (e + W on the FMA pipe) at 12 CTAs
+// per SM (40 registers, no spills): 0.534 -> 0.461 ms; at 16 CTAs per SM the
+// same code spills; 32-byte loads gave it nothing (0.459 ms).
+template <class H> struct AlignedForm;
+template <> struct AlignedForm<Md5> {
+    using Hash = Md5Split<kPolAll1>;
+    static constexpr int kMinCtas = 16;
+};
 template <> struct AlignedForm<Sha1> {
     using Hash = Sha1Split<0xFFFFu>;
     static constexpr int kMinCtas = 12;
 };
 
-template <class H>
+template <class H, bool LOAD32>
 __global__ void __launch_bounds__(128, AlignedForm<H>::kMinCtas)
     k_hash_blocks_aligned(const uint8_t *__restrict__ in, uint64_t block, uint64_t nfull,
                           uint8_t *__restrict__ out, uint32_t one) {
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < nfull) hash_aligned_block<typename AlignedForm<H>::Hash>(in, block, i, out, one);
+    if (i < nfull) hash_aligned_block<typename AlignedForm<H>::Hash, LOAD32>(in, block, i, out, one);
 }
 
 // Few blocks (fewer chains than it takes to fill the integer pipes): each
@@ -183,8 +211,13 @@ int launch_hash_blocks(int algo, const uint8_t *d_in, uint64_t n, uint64_t block
         const uint64_t nfull = n / block;
         if (nfull >= kFewChains) {
             const unsigned grid = (unsigned)((nfull + 127) / 128);
-            if (algo == HG_MD5) k_hash_blocks_aligned<Md5><<<grid, 128, 0, s>>>(d_in, block, nfull, d_digests, 1u);
-            else k_hash_blocks_aligned<Sha1><<<grid, 128, 0, s>>>(d_in, block, nfull, d_digests, 1u);
+            const bool a32 = (reinterpret_cast<uintptr_t>(d_in) & 31) == 0;
+            if (algo == HG_MD5 && a32)
+                k_hash_blocks_aligned<Md5, true><<<grid, 128, 0, s>>>(d_in, block, nfull, d_digests, 1u);
+            else if (algo == HG_MD5)
+                k_hash_blocks_aligned<Md5, false><<<grid, 128, 0, s>>>(d_in, block, nfull, d_digests, 1u);
+            else
+                k_hash_blocks_aligned<Sha1, false><<<grid, 128, 0, s>>>(d_in, block, nfull, d_digests, 1u);
         } else if (nfull) {
             const uint32_t lanes = nfull <= kHalfWarpChainsMax ? 16 : 32;
             const unsigned grid = chain_grid(nfull, lanes, 64);

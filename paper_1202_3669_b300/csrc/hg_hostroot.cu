@@ -209,12 +209,21 @@ void CUDART_CB root_host_fn(void *arg) {
 
 }  // namespace
 
-uint64_t host_root_min_bytes() {
-    static const uint64_t v = [] {
-        const char *env = std::getenv("HG_HOST_ROOT_MIN");
-        return env ? (uint64_t)std::strtoull(env, nullptr, 10) : kHostRootMinBytes;
+// Digest-list size from which the root is computed on the host. Measured on a
+// B300 machine (root time alone, host path including its copies and host-function
+// wake-up): the device chain runs MD5 at ~130 MB/s and SHA-1 at ~100 MB/s; a
+// host core ran MD5 at 70-650 MB/s depending on the box and on how long the
+// callback core had been idle, SHA-1 with the SHA extensions at ~1.1 GB/s
+// after ~0.08 ms of fixed cost. Crossovers: MD5 between 256 KiB and 1 MiB of
+// digests, SHA-1 (SHA extensions) near 10 KiB.
+uint64_t host_root_min_bytes(int algo) {
+    static const long long env = [] {
+        const char *e = std::getenv("HG_HOST_ROOT_MIN");
+        return e ? (long long)std::strtoull(e, nullptr, 10) : -1ll;
     }();
-    return v;
+    if (env >= 0) return (uint64_t)env;
+    if (algo == HG_MD5) return kHostRootMinMd5;
+    return use_sha_ni() ? kHostRootMinSha1Ni : kHostRootMinSha1;
 }
 
 int enqueue_host_root(hg_ctx *c, int algo, const uint8_t *d_digests, uint64_t nbytes, uint8_t *d_root,

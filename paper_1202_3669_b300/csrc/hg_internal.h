@@ -60,6 +60,9 @@ namespace hg {
 constexpr int kWinThreads = 256;
 constexpr int kWinPerThread = 32;
 constexpr uint64_t kWinTile = (uint64_t)kWinThreads * kWinPerThread;
+// The single-buffer MD5 window kernel runs one warp per CTA over a span of
+// kWinSpan window ends (an eighth of a tile).
+constexpr int kWinSpan = 32 * kWinPerThread;
 
 // Grid of a chain kernel whose tasks are dealt to `lanes` lanes of each warp
 // (see chain_task) for ntask tasks and `threads` threads per CTA.
@@ -198,10 +201,12 @@ __device__ __forceinline__ bool hg_dok(bool ok, int *err) {
 // hg_hostroot.cu: the library's host MD5/SHA-1, and the hash-of-hashes
 // computed on a host core in stream order (digests copied to pinned staging,
 // hashed by a host function, the root copied back). Digest lists shorter than
-// kHostRootMinBytes, and calls on a capturing stream, use the device chain.
-// HG_HOST_ROOT_MIN (bytes, read once) overrides the threshold.
-constexpr uint64_t kHostRootMinBytes = 8192;
-uint64_t host_root_min_bytes();
+// host_root_min_bytes(algo), and calls on a capturing stream, use the device
+// chain.
+// HG_HOST_ROOT_MIN (bytes, read once) overrides the thresholds.
+constexpr uint64_t kHostRootMinMd5 = 1ull << 20, kHostRootMinSha1Ni = 16ull << 10,
+                   kHostRootMinSha1 = 256ull << 10;
+uint64_t host_root_min_bytes(int algo);
 void host_digest(int algo, const uint8_t *msg, uint64_t n, uint8_t *out);
 int enqueue_host_root(hg_ctx *c, int algo, const uint8_t *d_digests, uint64_t nbytes, uint8_t *d_root,
                       cudaStream_t s);

@@ -14,13 +14,13 @@ constexpr int kSmemBytes = kHalo + (int)kWinTile + 16; // + a zeroed 16-byte pad
 constexpr long kWaitLimit = 1L << 22;                  // bounded mbarrier polling
 // Pipe policies of the window hash's constant-word and data-word steps: the
 // constant-word steps (42 of the 61) move both adds to the FMA pipe, the
-// data-word steps keep theirs on the ALU. Measured on a 64 MiB window pass
-// (ncu, 20-byte window): 0.688 -> 0.650 ms, ALU-pipe instructions per window
-// 191 -> 149, FMA-pipe 20 -> 104. Moving the data-word steps' adds as well, or
-// only the off-chain add, measured slower (0.66-0.71 ms): with both pipes
-// partly busy the kernel becomes issue- and dependency-limited (issue active
-// 70 %, math-pipe-throttle and barrier stalls).
-constexpr uint32_t kWinPolConst = kPolAll2, kWinPolData = kPolAllPlain;
+// data-word steps move the add of the logic op's result (policy 1). Measured
+// on a 64 MiB pass (20-byte window), one-warp CTAs: 0.616 ms, against 0.630
+// with the data-word adds left on the ALU, 0.682 with every add on the ALU,
+// 0.74-0.76 with policies 2/3 on the data-word steps. (In eight-warp CTAs at
+// 32 registers the constant-word split alone took 0.688 -> 0.651 ms, ALU-pipe
+// instructions per window 191 -> 149, FMA-pipe 20 -> 104.)
+constexpr uint32_t kWinPolConst = kPolAll2, kWinPolData = kPolAll1;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -136,9 +136,10 @@ __device__ __forceinline__ uint32_t window_bits32(const uint8_t *sbuf, int t, ui
     constexpr int NW = W ? (W + 3) / 4 : 1;
     constexpr int OFF = kHalo - (W ? W - 1 : 0);      // local byte of window 0's start
     constexpr int B0 = OFF / 4, R0 = OFF % 4;
-    // the last thread's last word read stays inside the staged tile + zero pad
-    static_assert(W == 0 || 8 * (kWinThreads - 1) + B0 + 7 + NW + 2 < kSmemBytes / 4,
-                  "window words read past the staged tile");
+    // With T threads the buffer holds kHalo + 32T + 16 bytes and thread T-1 reads
+    // words up to 8(T-1) + B0 + 7 + NW + 2: inside the buffer for every T exactly
+    // when B0 + NW + 1 < kHalo/4 + 4.
+    static_assert(W == 0 || B0 + NW + 1 < kHalo / 4 + 4, "window words read past the staged bytes");
     uint32_t bits = 0;
     if constexpr (W > 0) {
         const uint32_t *sw = reinterpret_cast<const uint32_t *>(sbuf);
