@@ -341,7 +341,8 @@ int hg_stream_destroy(hg_cdc_stream *st);
  */
 typedef struct hg_batch hg_batch;
 typedef struct {
-    int32_t window_ctas_per_sm;   /* persistent window kernel CTAs per SM */
+    int32_t window_ctas_per_sm;   /* persistent window kernel CTAs per SM; 0 = one-warp CTAs
+                                     over the tiles' 1024-window spans (MD5 window) */
     int32_t hash_threads;         /* chunk-hash kernel threads per CTA (32..512, power of 2) */
     int32_t hash_ctas_per_sm;     /* chunk-hash kernel CTAs per SM */
     int32_t reserved;
@@ -360,7 +361,7 @@ int hg_batch_sync(hg_batch *batch, void *stream);
 int hg_batch_get_tuning(const hg_batch *batch, hg_batch_tuning *tuning);
 int hg_batch_set_tuning(hg_batch *batch, const hg_batch_tuning *tuning);
 /* Time a small set of tunings on this batch (synchronous: runs the batch about
- * 60 times) and keep the fastest; it is also written to *best if not NULL. */
+ * 63 times) and keep the fastest; it is also written to *best if not NULL. */
 int hg_batch_autotune(hg_batch *batch, int algo, const uint8_t *d_data, uint64_t *d_ends,
                       uint64_t *d_counts, uint8_t *d_digests, void *stream, hg_batch_tuning *best);
 /* hg_batch_autotune through a cache file (JSON Lines, one

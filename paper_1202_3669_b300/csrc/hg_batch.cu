@@ -97,7 +97,7 @@ int hg_batch_create(hg_ctx *ctx, const uint64_t *h_file_off, uint32_t nfile,
     }
     if (rc == HG_OK) {
         b->win_max_per_sm = job_window_occupancy(p->window);
-        b->tune.window_ctas_per_sm = b->win_max_per_sm;
+        b->tune.window_ctas_per_sm = 0;           // one-warp span CTAs (MD5 window)
         // one warp per scheduler: a SHA-1 warp alone saturates its scheduler's
         // ALU pipe, so long chains run fastest without neighbours
         b->tune.hash_threads = 32;
@@ -142,7 +142,7 @@ int hg_batch_get_tuning(const hg_batch *b, hg_batch_tuning *t) {
 }
 
 int hg_batch_set_tuning(hg_batch *b, const hg_batch_tuning *t) {
-    if (!b || !t || t->window_ctas_per_sm < 1 || t->hash_ctas_per_sm < 1 ||
+    if (!b || !t || t->window_ctas_per_sm < 0 || t->hash_ctas_per_sm < 1 ||
         (t->hash_threads != 32 && t->hash_threads != 64 && t->hash_threads != 128 &&
          t->hash_threads != 256 && t->hash_threads != 512) || t->long_chunk_bytes == 0)
         return HG_EINVAL;
@@ -230,7 +230,7 @@ int hg_batch_autotune(hg_batch *b, int algo, const uint8_t *d_data, uint64_t *d_
     int rc = HG_OK;
     // window persistence first (the dominant kernel), then the chunk-hash shape
     const int wm = b->win_max_per_sm;
-    for (int w : {wm, std::max(1, wm * 3 / 4), std::max(1, wm / 2)}) {
+    for (int w : {0, wm, std::max(1, wm * 3 / 4), std::max(1, wm / 2)}) {
         cur = top;
         cur.window_ctas_per_sm = w;
         b->tune = cur;
@@ -296,7 +296,7 @@ static bool tune_lookup(const char *path, const std::string &key, hg_batch_tunin
                         "{\"window_ctas_per_sm\": %d, \"hash_threads\": %d, \"hash_ctas_per_sm\": %d, "
                         "\"long_chunk_bytes\": %llu}",
                         &w, &ht, &hc, &lb) == 4 &&
-            w >= 1 && ht >= 32 && ht <= 512 && hc >= 1) {
+            w >= 0 && ht >= 32 && ht <= 512 && hc >= 1) {
             *t = hg_batch_tuning{w, ht, hc, 0, lb};
             found = true;               // the last matching line wins
         }

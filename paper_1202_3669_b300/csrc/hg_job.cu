@@ -147,6 +147,58 @@ __global__ void __launch_bounds__(kWinThreads) k_job_window(JobDev j, uint32_t w
     }
 }
 
+// The same window test in one-warp CTAs (the form of the single-buffer window
+// kernel): CTA b takes span b % 8 (1024 window ends) of global tile b / 8, of
+// whichever file owns the tile; spans past the file's end write zero words.
+// Counts are added to the tile's count (zeroed before the launch). Selected by
+// the tuning's window_ctas_per_sm = 0.
+template <int W>
+__global__ void __launch_bounds__(32, 32) k_job_window_span(JobDev j, uint32_t wrt, uint32_t mask,
+                                                            uint32_t magic,
+                                                            uint32_t *__restrict__ bitmap,
+                                                            uint32_t *__restrict__ tile_cnt, int *err,
+                                                            uint32_t one) {
+    const uint32_t wlen = W ? (uint32_t)W : wrt;
+    constexpr int kSub = (int)(kWinTile / kWinSpan);
+    __shared__ __align__(128) uint8_t sbuf[kHalo + kWinSpan + 16];
+    __shared__ __align__(8) uint64_t mbar;
+    const int t = threadIdx.x;
+    const uint32_t tile = blockIdx.x / kSub, sub = blockIdx.x % kSub;
+    if (!HG_DOK(tile < j.ntiles, err)) return;
+    const TileRef r = tile_ref(j, tile);
+    const uint64_t lo = r.lo + (uint64_t)sub * kWinSpan;
+    uint32_t bits = 0;
+    if (lo < r.len) {
+        const bool fast = ((reinterpret_cast<uintptr_t>(r.ptr) & 15) == 0) && lo >= (uint64_t)kHalo &&
+                          lo + kWinSpan <= r.len;
+        if (t < 4) reinterpret_cast<uint32_t *>(sbuf + kHalo + kWinSpan)[t] = 0;
+        bool timed_out = false;
+        if (fast) {
+            const uint32_t mb = smem_u32(&mbar);
+            if (t == 0) mbar_init(mb);
+            __syncwarp();
+            if (t == 0) bulk_load(smem_u32(sbuf), r.ptr + lo - kHalo, (uint32_t)(kHalo + kWinSpan), mb);
+            timed_out = !mbar_wait(mb, 0);
+            if (timed_out) {
+                atomicCAS(err, 0, (int)HG_ETIMEDOUT);
+                mbar_wait(mb, 0);
+            }
+        } else {
+            for (int i = t; i < kHalo + kWinSpan; i += 32) {
+                const int64_t g = (int64_t)lo - kHalo + i;
+                sbuf[i] = (g >= 0 && (uint64_t)g < r.len) ? r.ptr[g] : (uint8_t)0;
+            }
+        }
+        if (__any_sync(0xffffffffu, timed_out)) return;
+        __syncwarp();
+        bits = clip_bits(window_bits32<W>(sbuf, t, wlen, mask, magic, one), lo + 32u * (uint64_t)t,
+                         wlen, r.len);
+    }
+    bitmap[(uint64_t)tile * kWinThreads + sub * 32 + t] = bits;
+    const uint32_t c = __reduce_add_sync(0xffffffffu, (uint32_t)__popc(bits));
+    if (t == 0 && c) atomicAdd(&tile_cnt[tile], c);
+}
+
 // Tile bitmap -> candidate cuts local to the tile's file, at the tile's scanned offset.
 __global__ void __launch_bounds__(kWinThreads) k_job_compact(JobDev j,
                                                              const uint32_t *__restrict__ bitmap,
@@ -387,6 +439,13 @@ void launch_job_window_t(int grid, const JobDev &j, uint32_t w, uint32_t mask, u
 }
 
 template <int W>
+void launch_job_window_span_t(const JobDev &j, uint32_t w, uint32_t mask, uint32_t magic,
+                              uint32_t *bm, uint32_t *tc, int *err, cudaStream_t s) {
+    const uint64_t spans = (uint64_t)j.ntiles * (kWinTile / kWinSpan);
+    k_job_window_span<W><<<(unsigned)spans, 32, 0, s>>>(j, w, mask, magic, bm, tc, err, 1u);
+}
+
+template <int W>
 int occupancy_t() {
     int nb = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_job_window<W>, kWinThreads, 0);
@@ -480,6 +539,18 @@ int enqueue_cdc_job(const JobDev &j, const JobScratch &sc, const hg_cdc_params &
 #undef HG_JR
                 default:
                     launch_job_rabin_t<0>(rgrid, j, p.window, mask, p.magic, sc.bitmap, sc.tile_cnt, s);
+            }
+        } else if (tn.window_ctas == 0) {
+            // one-warp CTAs over the tiles' spans; their counts are added up
+            if (cudaMemsetAsync(sc.tile_cnt, 0, (size_t)j.ntiles * 4, s) != cudaSuccess) return HG_ECUDA;
+            switch (p.window) {
+#define HG_JS(w)                                                                                \
+    case w: launch_job_window_span_t<w>(j, w, mask, p.magic, sc.bitmap, sc.tile_cnt, sc.err, s); break;
+                HG_JS(16) HG_JS(20) HG_JS(24) HG_JS(32) HG_JS(48)
+#undef HG_JS
+                default:
+                    launch_job_window_span_t<0>(j, p.window, mask, p.magic, sc.bitmap, sc.tile_cnt,
+                                                sc.err, s);
             }
         } else switch (p.window) {
 #define HG_JW(w)                                                                                \

@@ -316,7 +316,7 @@ int hg_server_create(hg_ctx *ctx, const hg_server_config *cfg, hg_server **out) 
     if (rc == HG_OK) {
         S->alloc.init(arena_bytes);
         ctx->held += cfg->device_budget;
-        S->tune = JobTuning{job_window_occupancy(p.window), 32, 8, 16384};
+        S->tune = JobTuning{0, 32, 8, 16384};       // one-warp window span CTAs
         S->th = std::thread(progress, S);
     }
     cudaSetDevice(prev);
