@@ -35,33 +35,20 @@ __device__ __forceinline__ void ld32(const uint8_t *p, uint32_t *v) {
                  : "l"(p));
 }
 
-// LOAD32: two 32-byte loads per 64-byte block (the input is 32-byte aligned):
-// a thread's loads touch one 128-byte line each, so a warp load costs 32 L1
-// wavefronts for 1 KiB instead of 512 bytes (the 16-byte form is bound by L1
-// tag throughput on MD5).
-template <class H, bool LOAD32>
+template <class H>
 __device__ __forceinline__ void hash_aligned_block(const uint8_t *__restrict__ in, uint64_t block,
                                                    uint64_t i, uint8_t *__restrict__ out,
                                                    uint32_t one) {
-    const uint8_t *base = in + i * block;
-    const uint4 *p = reinterpret_cast<const uint4 *>(base);
+    const uint4 *p = reinterpret_cast<const uint4 *>(in + i * block);
     const uint64_t nb = block >> 6;
     H hs;
     hs.init();
     hs.set_one(one);
     for (uint64_t k = 0; k < nb; k++) {
-        uint32_t M[16];
-        if constexpr (LOAD32) {
-            ld32(base + 64 * k, M);
-            ld32(base + 64 * k + 32, M + 8);
-        } else {
-            const uint4 x0 = __ldg(p + 4 * k), x1 = __ldg(p + 4 * k + 1);
-            const uint4 x2 = __ldg(p + 4 * k + 2), x3 = __ldg(p + 4 * k + 3);
-            M[0] = x0.x; M[1] = x0.y; M[2] = x0.z; M[3] = x0.w;
-            M[4] = x1.x; M[5] = x1.y; M[6] = x1.z; M[7] = x1.w;
-            M[8] = x2.x; M[9] = x2.y; M[10] = x2.z; M[11] = x2.w;
-            M[12] = x3.x; M[13] = x3.y; M[14] = x3.z; M[15] = x3.w;
-        }
+        const uint4 x0 = __ldg(p + 4 * k), x1 = __ldg(p + 4 * k + 1);
+        const uint4 x2 = __ldg(p + 4 * k + 2), x3 = __ldg(p + 4 * k + 3);
+        const uint32_t M[16] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w,
+                                x2.x, x2.y, x2.z, x2.w, x3.x, x3.y, x3.z, x3.w};
         hs.compress(M);
     }
     uint32_t Z[16] = {0x80u, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
@@ -70,14 +57,14 @@ __device__ __forceinline__ void hash_aligned_block(const uint8_t *__restrict__ i
     store_digest(hs, out + i * H::kDigest);
 }
 
-// Many blocks: the throughput form. MD5 is capped at 32 registers so 2048
-// threads fit an SM: with one chain per thread, occupancy is what hides the
-// loads (measured 4.1 vs 3.3 TB/s for the same loop at 37 registers); it runs
-// Md5Split with pipe policy 1 (the logic op's add on the FMA pipe) and, on a
-// 32-byte aligned input, 32-byte loads: 1 GiB in 4 KiB blocks 0.248 -> 0.239 ms.
-// SHA-1 runs Sha1Split with pipe policy 3 (e + W on the FMA pipe) at 12 CTAs
-// per SM (40 registers, no spills): 0.534 -> 0.461 ms; at 16 CTAs per SM the
-// same code spills; 32-byte loads gave it nothing (0.459 ms).
+// Many blocks: the throughput form, one chain per thread, 16-byte loads. MD5
+// is capped at 32 registers so 2048 threads fit an SM (occupancy is what hides
+// the loads: 4.1 vs 3.3 TB/s at 37 registers) and runs Md5Split with pipe
+// policy 1 (the logic op's add on the FMA pipe); a 32-byte aligned input takes
+// k_hash_blocks_aligned_x2 instead. SHA-1 runs Sha1Split with pipe policy 3
+// (e + W on the FMA pipe) at 12 CTAs per SM (40 registers, no spills): 1 GiB in
+// 4 KiB blocks 0.534 -> 0.461 ms; at 16 CTAs per SM the same code spills, and
+// 32-byte loads gave it nothing (0.459 ms).
 template <class H> struct AlignedForm;
 template <> struct AlignedForm<Md5> {
     using Hash = Md5Split<kPolAll1>;
@@ -88,12 +75,54 @@ template <> struct AlignedForm<Sha1> {
     static constexpr int kMinCtas = 12;
 };
 
-template <class H, bool LOAD32>
+template <class H>
 __global__ void __launch_bounds__(128, AlignedForm<H>::kMinCtas)
     k_hash_blocks_aligned(const uint8_t *__restrict__ in, uint64_t block, uint64_t nfull,
                           uint8_t *__restrict__ out, uint32_t one) {
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < nfull) hash_aligned_block<typename AlignedForm<H>::Hash, LOAD32>(in, block, i, out, one);
+    if (i < nfull) hash_aligned_block<typename AlignedForm<H>::Hash>(in, block, i, out, one);
+}
+
+// MD5 on a 32-byte aligned input: two 256-bit loads per 64-byte block (the
+// 16-byte form is bound by L1 tag throughput: each lane's load touches its own
+// 128-byte line, so a warp load costs 32 wavefronts for 512 bytes) and two
+// blocks per thread, their compressions interleaved (two independent chains,
+// 63 registers, 8 CTAs/SM). 1 GiB in 4 KiB blocks: 0.248 ms with one block per
+// thread and 16-byte loads, 0.239 with 32-byte loads, 0.231 (4.64 TB/s) with
+// two blocks; an L2 prefetch 2-8 blocks ahead was slower (0.258-0.37 ms), and
+// the interleave gave SHA-1 nothing.
+template <class H>
+__global__ void __launch_bounds__(128, 8) k_hash_blocks_aligned_x2(const uint8_t *__restrict__ in,
+                                                                    uint64_t block, uint64_t nfull,
+                                                                    uint8_t *__restrict__ out,
+                                                                    uint32_t one) {
+    const uint64_t i0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * 2;
+    if (i0 >= nfull) return;
+    const bool two = i0 + 1 < nfull;
+    const uint8_t *p0 = in + i0 * block, *p1 = in + (two ? i0 + 1 : i0) * block;
+    const uint64_t nb = block >> 6;
+    H h0, h1;
+    h0.init();
+    h0.set_one(one);
+    h1.init();
+    h1.set_one(one);
+    for (uint64_t k = 0; k < nb; k++) {
+        uint32_t M0[16], M1[16];
+        ld32(p0 + 64 * k, M0);
+        ld32(p0 + 64 * k + 32, M0 + 8);
+        ld32(p1 + 64 * k, M1);
+        ld32(p1 + 64 * k + 32, M1 + 8);
+        h0.compress(M0);
+        h1.compress(M1);
+    }
+    uint32_t Z0[16] = {0x80u, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    uint32_t Z1[16] = {0x80u, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    H::put_length(Z0, block);
+    H::put_length(Z1, block);
+    h0.compress(Z0);
+    h1.compress(Z1);
+    store_digest(h0, out + i0 * H::kDigest);
+    if (two) store_digest(h1, out + (i0 + 1) * H::kDigest);
 }
 
 // Few blocks (fewer chains than it takes to fill the integer pipes): each
@@ -213,11 +242,12 @@ int launch_hash_blocks(int algo, const uint8_t *d_in, uint64_t n, uint64_t block
             const unsigned grid = (unsigned)((nfull + 127) / 128);
             const bool a32 = (reinterpret_cast<uintptr_t>(d_in) & 31) == 0;
             if (algo == HG_MD5 && a32)
-                k_hash_blocks_aligned<Md5, true><<<grid, 128, 0, s>>>(d_in, block, nfull, d_digests, 1u);
+                k_hash_blocks_aligned_x2<Md5Split<kPolAll1>><<<(unsigned)((nfull + 255) / 256), 128, 0, s>>>(
+                    d_in, block, nfull, d_digests, 1u);
             else if (algo == HG_MD5)
-                k_hash_blocks_aligned<Md5, false><<<grid, 128, 0, s>>>(d_in, block, nfull, d_digests, 1u);
+                k_hash_blocks_aligned<Md5><<<grid, 128, 0, s>>>(d_in, block, nfull, d_digests, 1u);
             else
-                k_hash_blocks_aligned<Sha1, false><<<grid, 128, 0, s>>>(d_in, block, nfull, d_digests, 1u);
+                k_hash_blocks_aligned<Sha1><<<grid, 128, 0, s>>>(d_in, block, nfull, d_digests, 1u);
         } else if (nfull) {
             const uint32_t lanes = nfull <= kHalfWarpChainsMax ? 16 : 32;
             const unsigned grid = chain_grid(nfull, lanes, 64);
