@@ -115,12 +115,17 @@ int hg_host_digest(int algo, const uint8_t *msg, uint64_t n, uint8_t *out);
 /*
  * Create a context on CUDA device `device`. `device_budget_bytes` caps the
  * scratch memory the context may hold (0 = 32 GiB). Scratch is allocated on
- * first use and grown as needed; hg_reserve() allocates it ahead of time.
+ * first use and grown as needed. Growing it synchronises the whole device
+ * (queued work may still use the old scratch: cudaDeviceSynchronize, then
+ * cudaFree and cudaMalloc), so a call that grows scratch is not asynchronous;
+ * hg_reserve() allocates the scratch for inputs up to a given size ahead of
+ * time, after which calls on such inputs never synchronise.
  */
 int hg_init(hg_ctx **out, int device, size_t device_budget_bytes);
 /* Free the context and all its scratch (synchronises its device first). */
 int hg_destroy(hg_ctx *ctx);
-/* Pre-allocate scratch for chunking inputs of up to max_bytes bytes. */
+/* Pre-allocate scratch for chunking inputs of up to max_bytes bytes (may
+ * synchronise the device once, see hg_init). HG_ENOMEM over the budget. */
 int hg_reserve(hg_ctx *ctx, uint64_t max_bytes);
 /* Synchronise `stream` and return (then clear) the device error word. */
 int hg_sync(hg_ctx *ctx, void *stream);
