@@ -69,6 +69,12 @@ PinnedPool *pool_of(hg_ctx *c) {
     return c->pinned;
 }
 
+// The pool if it exists (read under the same lock that guards its creation).
+PinnedPool *existing_pool(hg_ctx *c) {
+    std::lock_guard<std::mutex> lock(c->pinned_mu);
+    return c->pinned;
+}
+
 }  // namespace
 
 void pinned_destroy(hg_ctx *c) {
@@ -124,7 +130,7 @@ void *hg_alloc_pinned(hg_ctx *c, size_t bytes) {
 
 int hg_free_pinned(hg_ctx *c, void *p) {
     if (!c || !p) return HG_EINVAL;
-    PinnedPool *pp = c->pinned;
+    PinnedPool *pp = existing_pool(c);
     if (!pp) return HG_EINVAL;
     std::lock_guard<std::mutex> lock(pp->mu);
     auto o = pp->owned.find(p);
@@ -149,7 +155,7 @@ int hg_pinned_set_budget(hg_ctx *c, uint64_t bytes) {
 
 int hg_pinned_trim(hg_ctx *c) {
     if (!c) return HG_EINVAL;
-    PinnedPool *pp = c->pinned;
+    PinnedPool *pp = existing_pool(c);
     if (!pp) return HG_OK;
     std::lock_guard<std::mutex> lock(pp->mu);
     const uint64_t keep = pp->budget;
@@ -162,7 +168,7 @@ int hg_pinned_trim(hg_ctx *c) {
 int hg_pinned_stats(hg_ctx *c, hg_pinned_info *out) {
     if (!c || !out) return HG_EINVAL;
     *out = hg_pinned_info{};
-    PinnedPool *pp = c->pinned;
+    PinnedPool *pp = existing_pool(c);
     out->budget_bytes = pp ? pp->budget : kPinnedDefaultBudget;
     if (!pp) return HG_OK;
     std::lock_guard<std::mutex> lock(pp->mu);
