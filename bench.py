@@ -615,6 +615,8 @@ def main():
                "e2e": {"value": replica_throughput(nbytes, world, t_e2e_all), "unit": UNIT,
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                        "pinned_h2d_copy_GBps": h2d_gbps,
+                       "link_frac": replica_throughput(nbytes, world, t_e2e_all) / world / h2d_gbps,
+                       "bound": "host link: the pinned host-to-device copy rate measured in this run",
                        "pinned_from": "hg_alloc_pinned pool",
                        "pinned_pool": {"host_allocs": sum(x["host_allocs"] for x in pool_stats),
                                        "held_bytes": sum(x["held_bytes"] for x in pool_stats)}},
