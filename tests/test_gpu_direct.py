@@ -41,6 +41,26 @@ def test_blocks_small(hg, algo, n, block, offset):
     assert root.cpu().numpy().tobytes() == oroot
 
 
+# Enough blocks for the throughput kernels (148 x 512 = 75776 and up), an odd
+# count (the two-block MD5 kernel's last thread hashes one block) and a short
+# last block, at 32-byte (two-block MD5 kernel), 16-byte (one block per
+# thread) and 8-byte (generic kernel) alignment; the roots take the host path.
+@pytest.mark.parametrize("algo", ALGOS)
+@pytest.mark.parametrize("block,extra", [(128, 77), (4096, 1234)])
+@pytest.mark.parametrize("offset", [0, 16, 8])
+def test_blocks_throughput_forms(hg, algo, block, extra, offset):
+    nfull = 75777
+    n = nfull * block + extra
+    data = G.uniform_bytes(n, seed=block + extra)
+    d = to_device(data, offset)
+    assert d.data_ptr() % 32 == offset % 32
+    dg, root = hg.hash_blocks(d, block, algo)
+    hg.sync()
+    odg, oroot = oracle.hash_blocks(algo, data, block)
+    assert np.array_equal(dg.cpu().numpy(), odg)
+    assert root.cpu().numpy().tobytes() == oroot
+
+
 @pytest.mark.parametrize("algo", ALGOS)
 def test_config_direct_8mib(hg, algo):
     """8 MiB seeded uniform buffer, 2048 blocks of 4 KiB, digests + hash-of-hashes."""
