@@ -674,14 +674,37 @@ def direct_leg(hgb, ctx, dev, flush):
                          "frac": r["GBps"] / bound}
         return r
 
+    # read-only HBM stream (a reduction over the 1 GiB input), context for the digest kernels
+    ro = []
+    for i in range(6):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        data.view(torch.int64).sum()
+        b.record(s)
+        if i >= 2:
+            ro.append((a, b))
+    torch.cuda.synchronize()
+    res["hbm_read_only_GBps"] = (1 << 30) / (min(x.elapsed_time(y) for x, y in ro) / 1e3) / 1e9
+
     for algo, name in ((hgb.MD5, "md5"), (hgb.SHA1, "sha1")):
         dl = 16 if algo == hgb.MD5 else 20
         out = torch.empty(((1 << 30) // 4096, dl), dtype=torch.uint8, device=dev)
         rt = torch.empty(dl, dtype=torch.uint8, device=dev)
         opb = OPS_PER_BYTE_MD5 if algo == hgb.MD5 else OPS_PER_BYTE_SHA1
+        # the rate of one serial digest chain: one 16 MiB block, one lane
+        one = timed(lambda: ctx.hash_blocks(data[:16 << 20], 16 << 20, algo, root=False, out=out[:1]),
+                    reps=4, warm=1)
+        chain_rate = (16 << 20) / (one["ms"] / 1e3) / 1e9
+        res[f"{name}_chain_GBps_per_chain"] = chain_rate
         for block, label in ((4096, "4KiB"), (65536, "64KiB"), (1 << 20, "1MiB")):
-            res[f"{name}_{label}"] = with_bound(timed(
-                lambda: ctx.hash_blocks(data, block, algo, root=False, out=out)), opb)
+            r = with_bound(timed(lambda: ctx.hash_blocks(data, block, algo, root=False, out=out)), opb)
+            # with few blocks each is one serial chain: at most nblk chains at the single-chain rate
+            chain = ((1 << 30) // block) * chain_rate
+            if chain < r["roofline"]["peak_GBps"]:
+                r["roofline"] = {"bound": "chain latency", "peak_GBps": chain, "frac": r["GBps"] / chain,
+                                 "note": f"{(1 << 30) // block} chains x {chain_rate:.3f} GB/s per chain"}
+            res[f"{name}_{label}"] = r
         r = timed(lambda: ctx.hash_blocks(data, 4096, algo, root=True, out=out, root_out=rt),
                   reps=5, warm=2)
         r["root_ms"] = r["ms"] - res[f"{name}_4KiB"]["ms"]
@@ -692,7 +715,8 @@ def direct_leg(hgb, ctx, dev, flush):
         res[f"{name}_1MiB_two_level_4KiB"] = timed(
             lambda: ctx.hash_blocks_pmd(data, 1 << 20, 4096, algo, out=ids, seg_out=out))
     ctx.sync()
-    res["note"] = (f"1 GiB uniform bytes (seed 4); 262144 / 16384 / 1024 blocks; two-level = "
+    res["note"] = (f"1 GiB uniform bytes (seed 4); 262144 / 16384 / 1024 blocks; chain rate = one "
+                   f"16 MiB block digested by one lane; two-level = "
                    f"H(4 KiB segment digests) per 1 MiB block; HBM peak {peaks['hbm_gbs']} GB/s ({kind})")
     return res
 

@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(128) k_hash_seg(const uint8_t *__restrict__ in
     const uint64_t a = i ? ends[i - 1] : st->start0, b = ends[i];
     if (!HG_DOK(a <= b && b <= n, err)) return;
     H hs;
-    hash_range(in + a, b - a, hs);
+    hash_range_staged(in + a, b - a, hs, stage_ring_dyn());
     store_digest(hs, out + i * H::kDigest);
 }
 
@@ -381,7 +381,7 @@ __global__ void __launch_bounds__(128) k_hash_sorted(const uint8_t *__restrict__
         const uint64_t a = i ? ends[i - 1] : s0;
         if (!HG_DOK(i < cnt && a <= ends[i] && ends[i] <= n, err)) return;
         H hs;
-        hash_range(in + a, ends[i] - a, hs);
+        hash_range_staged(in + a, ends[i] - a, hs, stage_ring_dyn());
         store_digest(hs, out + i * H::kDigest);
         return;
     }
@@ -396,7 +396,7 @@ __global__ void __launch_bounds__(128) k_hash_sorted(const uint8_t *__restrict__
             const uint64_t a = i ? ends[i - 1] : s0;
             if (HG_DOK(i < cnt && a <= ends[i] && ends[i] <= n, err)) {
                 H hs;
-                hash_range(in + a, ends[i] - a, hs);
+                hash_range_staged(in + a, ends[i] - a, hs, stage_ring_dyn());
                 store_digest(hs, out + i * H::kDigest);
             }
         }
@@ -511,12 +511,16 @@ int launch_pipe_segment(const uint8_t *d_in, uint64_t n, uint64_t n_sel, const h
     if (!digests) return cuda_status(cudaGetLastError());
     cudaStreamWaitEvent(s_hash, ev_sel, 0);
     const unsigned grid = (unsigned)((max_chunks + 127) / 128 + (b.klong + 3) / 4);
-    if (algo == HG_MD5)
-        k_hash_seg<Md5Chain><<<grid, 128, 0, s_hash>>>(d_in, b.ends, b.st, seg, b.long_idx, b.klong,
-                                                       b.digests, n, b.err);
-    else
-        k_hash_seg<Sha1><<<grid, 128, 0, s_hash>>>(d_in, b.ends, b.st, seg, b.long_idx, b.klong,
-                                                   b.digests, n, b.err);
+    const size_t smem = stage_bytes(128);
+    if (algo == HG_MD5) {
+        if (allow_dyn_smem((const void *)k_hash_seg<Md5Chain>, smem) != cudaSuccess) return HG_ECUDA;
+        k_hash_seg<Md5Chain><<<grid, 128, smem, s_hash>>>(d_in, b.ends, b.st, seg, b.long_idx, b.klong,
+                                                          b.digests, n, b.err);
+    } else {
+        if (allow_dyn_smem((const void *)k_hash_seg<Sha1>, smem) != cudaSuccess) return HG_ECUDA;
+        k_hash_seg<Sha1><<<grid, 128, smem, s_hash>>>(d_in, b.ends, b.st, seg, b.long_idx, b.klong,
+                                                      b.digests, n, b.err);
+    }
     return cuda_status(cudaGetLastError());
 }
 
@@ -532,12 +536,16 @@ int launch_hash_sorted(const uint8_t *d_in, uint64_t n, uint64_t max_chunks, con
     const uint64_t bulk_ctas = (uint64_t)b.klong * kBulkCtasPerSm;
     const uint64_t need = ((max_chunks + 31) / 32 + 3) / 4;
     const unsigned grid = (unsigned)((b.klong + 3) / 4 + (need < bulk_ctas ? need : bulk_ctas));
-    if (algo == HG_MD5)
-        k_hash_sorted<Md5Chain><<<grid, 128, 0, s>>>(d_in, b.ends, b.st, b.tasks, b.klong, b.digests,
-                                                     n, b.err);
-    else
-        k_hash_sorted<Sha1><<<grid, 128, 0, s>>>(d_in, b.ends, b.st, b.tasks, b.klong, b.digests, n,
-                                                 b.err);
+    const size_t smem = stage_bytes(128);
+    if (algo == HG_MD5) {
+        if (allow_dyn_smem((const void *)k_hash_sorted<Md5Chain>, smem) != cudaSuccess) return HG_ECUDA;
+        k_hash_sorted<Md5Chain><<<grid, 128, smem, s>>>(d_in, b.ends, b.st, b.tasks, b.klong,
+                                                        b.digests, n, b.err);
+    } else {
+        if (allow_dyn_smem((const void *)k_hash_sorted<Sha1>, smem) != cudaSuccess) return HG_ECUDA;
+        k_hash_sorted<Sha1><<<grid, 128, smem, s>>>(d_in, b.ends, b.st, b.tasks, b.klong, b.digests,
+                                                    n, b.err);
+    }
     return cuda_status(cudaGetLastError());
 }
 

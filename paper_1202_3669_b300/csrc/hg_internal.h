@@ -182,6 +182,18 @@ int launch_select(const uint64_t *d_cands, const uint64_t *d_ncand, uint64_t can
 
 inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? HG_OK : HG_ECUDA; }
 
+// A kernel that takes more than the default 48 KiB of dynamic shared memory
+// (the staged chains' rings) needs its limit raised before the launch; the
+// call enqueues nothing, so it is also made while a stream is captured.
+// Largest per-CTA dynamic shared memory used for staging rings (sm_103a
+// allows 227 KiB a block; 256 threads' rings take 132 KiB).
+constexpr size_t kStageSmemMax = 160u * 1024u;
+inline cudaError_t allow_dyn_smem(const void *kernel, size_t bytes) {
+    return bytes > 48u * 1024u
+               ? cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)
+               : cudaSuccess;
+}
+
 // Debug build (HG_DEBUG, libhashgpu_debug.so): kernels check the index of a
 // global access that is not in range by construction alone; a failed check
 // records HG_EBOUNDS in the error word and the access is skipped. In the

@@ -352,7 +352,9 @@ __global__ void k_job_tasks(JobDev j, const uint64_t *__restrict__ ends,
     }
 }
 
-template <class H>
+// STAGED: the chains read through shared-memory rings (hash_range_staged);
+// CTAs too large for the rings to fit use hash_range.
+template <class H, bool STAGED>
 __global__ void k_job_hash(JobDev j, const uint64_t *__restrict__ ends,
                            const uint64_t *__restrict__ tasks, unsigned long long *words,
                            uint8_t *__restrict__ digests, int *err) {
@@ -373,7 +375,8 @@ __global__ void k_job_hash(JobDev j, const uint64_t *__restrict__ ends,
             const uint64_t lo = i ? ends[so + i - 1] : 0, hi = ends[so + i];
             if (!HG_DOK(lo <= hi && hi <= jlen(j, f), err)) continue;
             H hs;
-            hash_range(jptr(j, f) + lo, hi - lo, hs);
+            if constexpr (STAGED) hash_range_staged(jptr(j, f) + lo, hi - lo, hs, stage_ring_dyn());
+            else hash_range(jptr(j, f) + lo, hi - lo, hs);
             store_digest(hs, digests + (so + i) * H::kDigest);
         }
     }
@@ -585,12 +588,24 @@ int enqueue_cdc_job(const JobDev &j, const JobScratch &sc, const hg_cdc_params &
         k_job_tasks<<<j.nfile, 128, 0, s>>>(j, d_ends, d_counts, cursor, sc.tasks);
     }
     const int hgrid = num_sms * tn.hash_ctas;
-    if (algo == HG_MD5)
-        k_job_hash<Md5Chain><<<hgrid, tn.hash_threads, 0, s>>>(j, d_ends, sc.tasks, sc.words, d_digests,
-                                                                sc.err);
-    else
-        k_job_hash<Sha1><<<hgrid, tn.hash_threads, 0, s>>>(j, d_ends, sc.tasks, sc.words, d_digests,
-                                                            sc.err);
+    const size_t smem = stage_bytes((unsigned)tn.hash_threads);
+    if (smem <= kStageSmemMax) {
+        const void *k = algo == HG_MD5 ? (const void *)k_job_hash<Md5Chain, true>
+                                       : (const void *)k_job_hash<Sha1, true>;
+        if (allow_dyn_smem(k, smem) != cudaSuccess) return HG_ECUDA;
+        if (algo == HG_MD5)
+            k_job_hash<Md5Chain, true><<<hgrid, tn.hash_threads, smem, s>>>(j, d_ends, sc.tasks, sc.words,
+                                                                           d_digests, sc.err);
+        else
+            k_job_hash<Sha1, true><<<hgrid, tn.hash_threads, smem, s>>>(j, d_ends, sc.tasks, sc.words,
+                                                                       d_digests, sc.err);
+    } else if (algo == HG_MD5) {
+        k_job_hash<Md5Chain, false><<<hgrid, tn.hash_threads, 0, s>>>(j, d_ends, sc.tasks, sc.words,
+                                                                       d_digests, sc.err);
+    } else {
+        k_job_hash<Sha1, false><<<hgrid, tn.hash_threads, 0, s>>>(j, d_ends, sc.tasks, sc.words,
+                                                                   d_digests, sc.err);
+    }
     return cuda_status(cudaGetLastError());
 }
 
