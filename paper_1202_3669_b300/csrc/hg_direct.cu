@@ -127,20 +127,23 @@ __global__ void __launch_bounds__(128, 8) k_hash_blocks_aligned_x2(const uint8_t
 
 // Few blocks (fewer chains than it takes to fill the integer pipes): each
 // block is a latency-bound chain, so the chain form of the step, the message
-// staged through shared memory (hash_range_staged), no register cap, small
-// CTAs spread over the SMs, and half warps when the chains are very few
-// (chain_task). 1 GiB in 64 KiB blocks: 0.686 ms with one block loaded ahead
-// into registers.
+// staged through shared memory (hash_range_staged), no register cap, and
+// half warps in two-warp CTAs when the chains are very few (chain_task).
+// With more chains, full warps in four-warp CTAs: one CTA per SM puts one
+// warp on each scheduler, where a 32-lane MD5 chain warp keeps the ALU pipe
+// ~70 % busy by itself; with two-warp CTAs an SM that received several of
+// them ran two or three chain warps per scheduler (1 GiB in 64 KiB blocks:
+// 0.52 ms, or 1.03 ms when the CTAs bunched). With one block loaded ahead into
+// registers instead of staged: 0.686 ms.
 template <class H>
-__global__ void __launch_bounds__(64) k_hash_blocks_aligned_few(const uint8_t *__restrict__ in,
-                                                                uint64_t block, uint64_t nfull,
-                                                                uint32_t lanes,
-                                                                uint8_t *__restrict__ out) {
-    __shared__ __align__(16) uint4 ring[64 * kStageStride];
+__global__ void __launch_bounds__(128) k_hash_blocks_aligned_few(const uint8_t *__restrict__ in,
+                                                                 uint64_t block, uint64_t nfull,
+                                                                 uint32_t lanes,
+                                                                 uint8_t *__restrict__ out) {
     uint64_t i;
     if (!chain_task(i, lanes) || i >= nfull) return;
     H hs;
-    hash_range_staged(in + i * block, block, hs, ring + threadIdx.x * kStageStride);
+    hash_range_staged(in + i * block, block, hs, stage_ring_dyn());
     store_digest(hs, out + i * H::kDigest);
 }
 
@@ -259,13 +262,18 @@ int launch_hash_blocks(int algo, const uint8_t *d_in, uint64_t n, uint64_t block
                 k_hash_blocks_aligned<Sha1><<<grid, 128, 0, s>>>(d_in, block, nfull, d_digests, 1u);
         } else if (nfull) {
             const uint32_t lanes = nfull <= kHalfWarpChainsMax ? 16 : 32;
-            const unsigned grid = chain_grid(nfull, lanes, 64);
+            const unsigned threads = lanes == 16 ? 64 : 128;
+            const unsigned grid = chain_grid(nfull, lanes, threads);
+            const size_t smem = stage_bytes(threads);
+            const void *k = algo == HG_MD5 ? (const void *)k_hash_blocks_aligned_few<Md5Chain>
+                                           : (const void *)k_hash_blocks_aligned_few<Sha1>;
+            if (allow_dyn_smem(k, smem) != cudaSuccess) return HG_ECUDA;
             if (algo == HG_MD5)
-                k_hash_blocks_aligned_few<Md5Chain><<<grid, 64, 0, s>>>(d_in, block, nfull, lanes,
-                                                                      d_digests);
+                k_hash_blocks_aligned_few<Md5Chain><<<grid, threads, smem, s>>>(d_in, block, nfull,
+                                                                               lanes, d_digests);
             else
-                k_hash_blocks_aligned_few<Sha1><<<grid, 64, 0, s>>>(d_in, block, nfull, lanes,
-                                                                  d_digests);
+                k_hash_blocks_aligned_few<Sha1><<<grid, threads, smem, s>>>(d_in, block, nfull, lanes,
+                                                                           d_digests);
         }
         if (nfull < nblk) {
             const uint64_t lo = nfull * block;
