@@ -123,6 +123,34 @@ def test_hash_chunks_arbitrary(hg, algo):
     assert np.array_equal(dg.cpu().numpy(), oracle.hash_chunks(algo, data, ends.astype(np.uint64)))
 
 
+# Chunk digests read their message through shared-memory rings filled by
+# asynchronous copies of 16-byte granules: every start residue mod 16 (the
+# shift of the unaligned loop and the extra granule of the first group) with
+# lengths at and around the 64-byte block edges, empty chunks included.
+STAGED_LENGTHS = [0, 1, 15, 16, 55, 56, 63, 64, 65, 127, 128, 129, 191, 192, 255, 256, 257, 319,
+                  320, 321, 1000, 4095, 4096, 4097, 70_000]
+
+
+@pytest.mark.parametrize("algo", [oracle.MD5, oracle.SHA1])
+@pytest.mark.parametrize("offset", [0, 7])
+def test_hash_chunks_staged_edges(hg, algo, offset):
+    ends, cur = [], 0
+    for L in STAGED_LENGTHS:
+        for r in range(16):
+            pad = (r - (offset + cur)) % 16         # a spacer chunk to reach residue r
+            cur += pad
+            ends.append(cur)
+            cur += L
+            ends.append(cur)
+    ends = np.array(ends, dtype=np.uint64)
+    data = G.uniform_bytes(int(ends[-1]), seed=len(ends))
+    d = to_device(data, offset)
+    e = torch.from_numpy(ends.astype(np.int64)).cuda()
+    dg = hg.hash_chunks(d, e, algo)
+    hg.sync()
+    assert np.array_equal(dg.cpu().numpy(), oracle.hash_chunks(algo, data, ends))
+
+
 def test_boundaries_capacity_reports_count(hg):
     data = G.uniform_bytes(1 << 20, seed=12)
     want = oracle.cdc(data, nthreads=8)

@@ -22,9 +22,12 @@ def hg():
 
 
 ALGOS = [oracle.MD5, oracle.SHA1]
+# (4096 * 64, 64), (4097 * 128 + 5, 128), (320_010, 64): exactly 4096 aligned
+# blocks (half-warp chain layout) and just above it (four-warp CTAs)
 SMALL = [(0, 4096), (1, 4096), (55, 4096), (56, 64), (63, 4096), (64, 4096), (4096, 4096),
          (4097, 4096), (1_000_003, 4096), (300_000, 65536), (3 << 20, 1 << 20), (5000, 7),
-         (100_000, 64), (100_000, 100), (70_000, 120)]
+         (100_000, 64), (100_000, 100), (70_000, 120), (4096 * 64, 64), (4097 * 128 + 5, 128),
+         (320_010, 64)]
 
 
 @pytest.mark.parametrize("algo", ALGOS)
