@@ -521,6 +521,8 @@ def main():
         ev.append((a, b))
     torch.cuda.synchronize()
     t_e2e = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
+    stages = stage_breakdown(versions, streams, main_s, flush, h_in, d_in2, (ends, cnts, dgs),
+                             (h_ends, h_cnt, h_dg), e2e_step, t_dev, t_e2e)
     pool_stats = [c.pinned_stats() for c in ctxs]
     clocks = clk.stop()
     for c in ctxs:
@@ -619,7 +621,8 @@ def main():
                        "bound": "host link: the pinned host-to-device copy rate measured in this run",
                        "pinned_from": "hg_alloc_pinned pool",
                        "pinned_pool": {"host_allocs": sum(x["host_allocs"] for x in pool_stats),
-                                       "held_bytes": sum(x["held_bytes"] for x in pool_stats)}},
+                                       "held_bytes": sum(x["held_bytes"] for x in pool_stats)},
+                       "stages": stages},
                "gpu_launches": launches_per_step * args.steps,
                "roofline": roofline,
                "cdc_step_roofline": cdc_step_roofline,
@@ -634,6 +637,71 @@ def main():
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+# hg_cdc_hash_h2d copies an input of up to 480 MiB in 8 MiB pieces
+H2D_PIECE = 8 << 20
+
+
+def stage_breakdown(versions, streams, main_s, flush, h_in, d_in, dev_out, host_out, e2e_step,
+                    t_kernel_ms, t_e2e_ms, reps=10):
+    """Per-stage times of the e2e step, each stage alone (the paper's stage breakdown of a
+    GPU hashing call, Table 1 / Fig. 4: allocation, copy in, kernel, copy out, host work):
+    h2d = both versions' inputs host -> device in the library's pieces, each version on its
+    stream; kernel = the device-resident step timed above; d2h = the result copies alone;
+    host = the host time to enqueue one e2e step. Nothing is allocated inside the step (the
+    pinned pool and the reserved device scratch are reused), so the allocation stage is 0.
+    overlap_saved_ms = h2d + kernel + d2h - e2e; tail_after_h2d_ms = e2e - h2d."""
+    import torch
+    ends, cnts, dgs = dev_out
+    h_ends, h_cnt, h_dg = host_out
+
+    def fork(body):
+        ev0 = torch.cuda.Event()
+        ev0.record(main_s)
+        for i, s in enumerate(streams):
+            s.wait_event(ev0)
+            with torch.cuda.stream(s):
+                body(i)
+        for s in streams:
+            main_s.wait_stream(s)
+
+    def h2d(i):
+        for lo in range(0, versions[i].size, H2D_PIECE):
+            d_in[i][lo:lo + H2D_PIECE].copy_(h_in[i][lo:lo + H2D_PIECE], non_blocking=True)
+
+    def d2h(i):
+        h_cnt[i].copy_(cnts[i], non_blocking=True)
+        h_ends[i].copy_(ends[i], non_blocking=True)
+        h_dg[i].copy_(dgs[i], non_blocking=True)
+
+    def timed(body):
+        fork(body)
+        torch.cuda.synchronize()
+        ev = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(main_s)
+            fork(body)
+            b.record(main_s)
+            ev.append((a, b))
+        torch.cuda.synchronize()
+        return statistics.median(a.elapsed_time(b) for a, b in ev)
+
+    t_h2d, t_d2h = timed(h2d), timed(d2h)
+    host = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_step()
+        host.append((time.perf_counter() - t0) * 1e3)
+    torch.cuda.synchronize()
+    return {"alloc_ms": 0.0, "h2d_ms": t_h2d, "kernel_ms": t_kernel_ms, "d2h_ms": t_d2h,
+            "host_enqueue_ms": statistics.median(host), "e2e_ms": t_e2e_ms,
+            "overlap_saved_ms": t_h2d + t_kernel_ms + t_d2h - t_e2e_ms,
+            "tail_after_h2d_ms": t_e2e_ms - t_h2d,
+            "note": "each stage timed alone (CUDA events, median); h2d in 8 MiB pieces per version"}
 
 
 def direct_leg(hgb, ctx, dev, flush):
