@@ -87,12 +87,14 @@ __global__ void __launch_bounds__(128, AlignedForm<H>::kMinCtas)
 // 16-byte form is bound by L1 tag throughput: each lane's load touches its own
 // 128-byte line, so a warp load costs 32 wavefronts for 512 bytes) and two
 // blocks per thread, their compressions interleaved (two independent chains,
-// 63 registers, 8 CTAs/SM). 1 GiB in 4 KiB blocks: 0.248 ms with one block per
-// thread and 16-byte loads, 0.239 with 32-byte loads, 0.231 (4.64 TB/s) with
-// two blocks; an L2 prefetch 2-8 blocks ahead was slower (0.258-0.37 ms), and
-// the interleave gave SHA-1 nothing.
+// 63 registers, 8 CTAs/SM resident). 1 GiB in 4 KiB blocks: 0.248 ms with one
+// block per thread and 16-byte loads, 0.239 with 32-byte loads, 0.231 (4.64
+// TB/s) with two blocks; an L2 prefetch 2-8 blocks ahead was slower (0.258-0.37
+// ms), and the interleave gave SHA-1 nothing. Declared for 6 CTAs/SM: the same
+// 63 registers and residency, scheduled ~1.5 % faster than when declared for 8
+// (0.2294 vs 0.2315-0.2335 ms with L2 flushed; 4, 5 and 7 equal 6).
 template <class H>
-__global__ void __launch_bounds__(128, 8) k_hash_blocks_aligned_x2(const uint8_t *__restrict__ in,
+__global__ void __launch_bounds__(128, 6) k_hash_blocks_aligned_x2(const uint8_t *__restrict__ in,
                                                                     uint64_t block, uint64_t nfull,
                                                                     uint8_t *__restrict__ out,
                                                                     uint32_t one) {
