@@ -428,6 +428,10 @@ typedef struct {
     uint32_t max_wave_requests;   /* requests per wave (4096) */
     uint32_t max_inflight_waves;  /* waves on the GPU at once, 1..8 (3) */
     hg_cdc_params cdc;            /* chunking parameters of HG_REQ_CDC requests */
+    uint64_t wave_target_bytes;   /* a wave takes no further request once that would
+                                     bring its input past this many bytes; a single
+                                     larger request (up to max_wave_bytes) still forms
+                                     a wave of its own. 0: max_wave_bytes (256 MiB) */
 } hg_server_config;
 
 typedef struct {

@@ -341,7 +341,8 @@ class Server:
 
     def __init__(self, ctx: Context, device_budget: int | None = None,
                  max_wave_bytes: int | None = None, max_wave_requests: int | None = None,
-                 max_inflight_waves: int | None = None, p: hg_cdc_params | None = None):
+                 max_inflight_waves: int | None = None, p: hg_cdc_params | None = None,
+                 wave_target_bytes: int | None = None):
         cfg = hg_server_config()
         hg_server_default_config(cfg)
         if device_budget is not None:
@@ -352,6 +353,8 @@ class Server:
             cfg.max_wave_requests = max_wave_requests
         if max_inflight_waves is not None:
             cfg.max_inflight_waves = max_inflight_waves
+        if wave_target_bytes is not None:
+            cfg.wave_target_bytes = wave_target_bytes
         if p is not None:
             cfg.cdc = p
         self.cfg = cfg

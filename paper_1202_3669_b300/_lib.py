@@ -50,7 +50,7 @@ class hg_result(C.Structure):
 class hg_server_config(C.Structure):
     _fields_ = [("device_budget", C.c_uint64), ("max_wave_bytes", C.c_uint64),
                 ("max_wave_requests", C.c_uint32), ("max_inflight_waves", C.c_uint32),
-                ("cdc", hg_cdc_params)]
+                ("cdc", hg_cdc_params), ("wave_target_bytes", C.c_uint64)]
 
 
 class hg_pinned_info(C.Structure):

@@ -14,7 +14,8 @@
 //                 42.5 GB/s as one copy each against 55 GB/s for large
 //                 copies), larger or unmapped ones by one copy call each;
 //                 the wave's compute waits on the staging in-stream;
-//   waves      -- all requests admitted together run as one wave: one batched
+//   waves      -- the requests admitted together (until the wave's input
+//                 reaches wave_target_bytes) run as one wave: one batched
 //                 chunking job (hg_job.cu) for the chunking requests plus the
 //                 fixed-block kernels for the block requests, then one copy
 //                 of the wave's outputs to pinned host memory;
@@ -231,6 +232,7 @@ void hg_server_default_config(hg_server_config *c) {
     c->max_wave_requests = 4096;
     c->max_inflight_waves = 3;
     hg_cdc_default_params(&c->cdc);
+    c->wave_target_bytes = 256ull << 20;
 }
 
 int hg_server_create(hg_ctx *ctx, const hg_server_config *cfg, hg_server **out) {
@@ -686,12 +688,15 @@ static void progress(hg_server *S) {
             w.slot = slot;
             uint64_t bytes = 0, blk = 0, slots_used = 0;
             const hg_cdc_params &p = S->cfg.cdc;
+            const uint64_t wave_target = S->cfg.wave_target_bytes ? S->cfg.wave_target_bytes
+                                                                  : S->cfg.max_wave_bytes;
             while (!S->queue.empty() && w.reqs.size() < S->cfg.max_wave_requests) {
                 auto &q = S->queue.front();
                 const uint64_t ob = req_out_bytes(q->rq, p.min_chunk);
                 const bool cdc = q->rq.kind == HG_REQ_CDC;
                 const uint64_t ns = cdc ? (q->rq.n ? q->rq.n / p.min_chunk + 1 : 0) : 0;
                 if (bytes + q->rq.n > S->cfg.max_wave_bytes) break;
+                if (!w.reqs.empty() && bytes + q->rq.n > wave_target) break;
                 if (!cdc && blk + a256(ob) > S->max_blk_bytes) break;
                 if (cdc && slots_used + ns > S->max_slots_per_wave) break;
                 uint64_t off;

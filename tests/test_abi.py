@@ -51,6 +51,16 @@ def test_host_only_calls():
     assert (p.window, p.mask_bits, p.magic, p.min_chunk, p.max_chunk) == (20, 13, 0x0F0F, 2048, 65536)
 
 
+def test_server_default_config():
+    """Default server limits (host code): 1 GiB per wave at most, waves closed at 256 MiB."""
+    from paper_1202_3669_b300 import _lib
+    cfg = _lib.hg_server_config()
+    _lib.lib.hg_server_default_config(C.byref(cfg))
+    assert C.sizeof(cfg) == 64
+    assert (cfg.device_budget, cfg.max_wave_bytes, cfg.wave_target_bytes) == (32 << 30, 1 << 30, 256 << 20)
+    assert (cfg.max_wave_requests, cfg.max_inflight_waves, cfg.cdc.window) == (4096, 3, 20)
+
+
 def test_init_without_gpu_fails_cleanly():
     import torch
     if torch.cuda.is_available():

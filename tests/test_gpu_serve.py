@@ -81,6 +81,28 @@ def test_mix_equals_alone_and_oracle(hg):
         assert a["t_submit_ns"] <= a["t_admit_ns"] <= a["t_done_ns"]
 
 
+def test_wave_target_splits_waves_and_keeps_results(hg):
+    """A small per-wave byte target closes waves early (more, smaller waves); a request
+    larger than the target but within max_wave_bytes still runs, in a wave of its own.
+    Results are unchanged."""
+    import paper_1202_3669_b300 as hgb
+    reqs = mixed_requests(40, seed=11)
+    reqs.append((G.uniform_bytes((3 << 20) + 5, 999), hgb.HG_REQ_CDC, hgb.MD5, 0, False))
+    total = sum(r[0].size for r in reqs)
+    target = 1 << 20
+    srv = hgb.Server(hg, device_budget=2 << 30, max_wave_bytes=64 << 20, wave_target_bytes=target)
+    assert srv.cfg.wave_target_bytes == target
+    tickets = [srv.submit(*r) for r in reqs]
+    res = [srv.poll(t) for t in tickets]
+    st = srv.stats()
+    srv.close()
+    for r, x in zip(reqs, res):
+        check_result(r, x)
+    # every wave but those holding one large request carries at most `target` bytes
+    assert st["waves"] >= total // (target + (6 << 20))
+    assert st["completed"] == len(reqs)
+
+
 def test_admission_under_small_budget(hg):
     """The arena holds only a few requests at once; everything still completes exactly."""
     import paper_1202_3669_b300 as hgb
