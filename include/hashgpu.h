@@ -387,7 +387,7 @@ int hg_batch_autotune_cached(hg_batch *batch, int algo, const uint8_t *d_data, u
  * computation). One progress thread per server admits requests in arrival
  * order while their input fits in a device arena of device_budget bytes
  * (allocated once at creation, with the per-wave scratch carved from the same
- * budget), copies them to the device on a copy stream (inputs up to 512 KiB
+ * budget), copies them to the device on a copy stream (inputs up to 2 MiB
  * that lie in pinned host memory the device has mapped are pulled by one
  * gather kernel per wave instead of one copy call each), and runs everything
  * admitted together as one wave: one batched chunking job for the chunking

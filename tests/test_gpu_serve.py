@@ -179,18 +179,19 @@ def test_replay_trace(hg):
 
 def test_pinned_inputs_gathered_by_kernel(hg):
     """Inputs in pinned host memory (slices at odd offsets of one pinned pool, as a
-    service would hold them) take the gather kernel below 512 KiB and copy calls
-    above; both land exactly."""
+    service would hold them, starting at every residue mod 16) take the gather
+    kernel up to 2 MiB (in 256 KiB pieces) and copy calls above; both land exactly."""
     import paper_1202_3669_b300 as hgb
     pool_np = G.uniform_bytes(24 << 20, seed=901)
     pool = torch.from_numpy(pool_np).pin_memory()
     g = np.random.default_rng(902)
     sizes = [1, 2, 3, 4, 5, 63, 64, 65, 4095, 4097, 100_000, 511 << 10, 512 << 10, (512 << 10) + 1,
-             3 << 20] + g.integers(1, 600_000, 40).tolist()
+             (256 << 10) + 17, (2 << 20) - 1, 2 << 20, (2 << 20) + 1, 3 << 20] + g.integers(1, 600_000, 40).tolist()
     srv = hgb.Server(hg, device_budget=1 << 30, max_wave_bytes=32 << 20, max_wave_requests=64)
     reqs = []
     for i, z in enumerate(sizes):
-        off = int(g.integers(0, pool_np.size - z))
+        off = int(g.integers(0, pool_np.size - z - 16))
+        off += (i - off) % 16                          # every start residue mod 16 in turn
         view = pool[off:off + z]
         kind = hgb.HG_REQ_CDC if i % 3 else hgb.HG_REQ_BLOCKS
         reqs.append((pool_np[off:off + z], view, kind))
