@@ -60,6 +60,12 @@ ISSUE_LANES_PER_SM_CLK = 128
 # 64 bytes), so the whole chunking step costs about 275 operations per input byte.
 OPS_PER_BYTE_CDC_STEP = OPS_PER_WINDOW + 5.1
 OPS_PER_BYTE_MD5, OPS_PER_BYTE_SHA1 = 5.1, 9.6
+# Instructions per 64-byte block that only the integer ALU pipe runs, whatever the adds'
+# placement: MD5 one logic op and one rotate-add per step (64 steps); SHA-1 80 logic ops,
+# 80 rotate-adds, 80 rotates of b, 64 x 3 schedule ops (two 3-input XORs, a rotate) and
+# 16 byte swaps. Against the ALU pipe's 64 lanes per SM per clock they bound the block
+# kernels whatever is moved to the FMA pipe (a secondary roofline beside the issue rate's).
+ALU_ONLY_PER_BLOCK_MD5, ALU_ONLY_PER_BLOCK_SHA1 = 128, 448
 # The integer ALU pipe alone (logic, funnel shift, rotate-add issue only there) takes
 # one warp instruction every other clock per scheduler: 64 lanes per SM per clock.
 ALU_LANES_PER_SM_CLK = 64
@@ -735,11 +741,17 @@ def direct_leg(hgb, ctx, dev, flush):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     issue = sms * ISSUE_LANES_PER_SM_CLK * float(peaks.get("sm_max_mhz", 2032.0)) * 1e6
 
-    def with_bound(r, ops_per_byte):
+    alu_pipe = sms * ALU_LANES_PER_SM_CLK * float(peaks.get("sm_max_mhz", 2032.0)) * 1e6
+
+    def with_bound(r, ops_per_byte, alu_only_per_block):
         alu = issue / ops_per_byte / 1e9
         bound = min(peaks["hbm_gbs"], alu)
         r["roofline"] = {"bound": "hbm" if peaks["hbm_gbs"] <= alu else "alu", "peak_GBps": bound,
                          "frac": r["GBps"] / bound}
+        # secondary: the ALU pipe alone, on the instructions nothing else can run
+        pipe = alu_pipe / (alu_only_per_block / 64.0) / 1e9
+        r["roofline"]["alu_pipe_bound_GBps"] = pipe
+        r["roofline"]["frac_of_alu_pipe_bound"] = r["GBps"] / pipe
         return r
 
     # read-only HBM stream (a reduction over the 1 GiB input), context for the digest kernels
@@ -760,13 +772,14 @@ def direct_leg(hgb, ctx, dev, flush):
         out = torch.empty(((1 << 30) // 4096, dl), dtype=torch.uint8, device=dev)
         rt = torch.empty(dl, dtype=torch.uint8, device=dev)
         opb = OPS_PER_BYTE_MD5 if algo == hgb.MD5 else OPS_PER_BYTE_SHA1
+        aob = ALU_ONLY_PER_BLOCK_MD5 if algo == hgb.MD5 else ALU_ONLY_PER_BLOCK_SHA1
         # the rate of one serial digest chain: one 16 MiB block, one lane
         one = timed(lambda: ctx.hash_blocks(data[:16 << 20], 16 << 20, algo, root=False, out=out[:1]),
                     reps=4, warm=1)
         chain_rate = (16 << 20) / (one["ms"] / 1e3) / 1e9
         res[f"{name}_chain_GBps_per_chain"] = chain_rate
         for block, label in ((4096, "4KiB"), (65536, "64KiB"), (1 << 20, "1MiB")):
-            r = with_bound(timed(lambda: ctx.hash_blocks(data, block, algo, root=False, out=out)), opb)
+            r = with_bound(timed(lambda: ctx.hash_blocks(data, block, algo, root=False, out=out)), opb, aob)
             # with few blocks each is one serial chain: at most nblk chains at the single-chain rate
             chain = ((1 << 30) // block) * chain_rate
             if chain < r["roofline"]["peak_GBps"]:
