@@ -6,7 +6,10 @@ raw C functions are re-exported under their C names from `_lib`.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes as C
+import sys
+import weakref
 
 import numpy as np
 import torch
@@ -30,6 +33,27 @@ from ._lib import (HG_MD5, HG_SHA1, HashGPUError, check, default_params,  # noqa
 
 MD5, SHA1 = HG_MD5, HG_SHA1
 DIGEST_LEN = {MD5: 16, SHA1: 20}
+
+# Library objects still open when the interpreter exits are closed by an exit
+# handler, servers, streams, block maps and batches before the contexts they were
+# made on, while the CUDA runtime and this module are still intact. Finalizers that
+# run later, during interpreter teardown, do not call into the library.
+_children: "weakref.WeakSet" = weakref.WeakSet()
+_contexts: "weakref.WeakSet" = weakref.WeakSet()
+
+
+@atexit.register
+def _close_all() -> None:
+    for group in (_children, _contexts):
+        for obj in list(group):
+            try:
+                obj._release()
+            except Exception:
+                pass
+
+
+def _finalizer_may_call() -> bool:
+    return not sys.is_finalizing()
 
 
 WIN_MD5, WIN_RABIN = 0, 1
@@ -99,6 +123,7 @@ class Context:
         self.device = torch.device("cuda", device)
         self.h = hg_init(device, budget)
         self._pinned = set()
+        _contexts.add(self)
 
     def close(self):
         if getattr(self, "h", None):
@@ -124,9 +149,13 @@ class Context:
     def trim_pinned(self) -> None:
         check(hg_pinned_trim(self.h), "hg_pinned_trim")
 
+    def _release(self):
+        self.close()
+
     def __del__(self):
         try:
-            self.close()
+            if _finalizer_may_call():
+                self.close()
         except Exception:
             pass
 
@@ -266,6 +295,7 @@ class Batch:
         self.file_off = np.ascontiguousarray(file_off, dtype=np.uint64)
         self.nfile = self.file_off.size - 1
         self.h = hg_batch_create(ctx.h, self.file_off.ctypes.data, self.nfile, self.p)
+        _children.add(self)
         self.slot_off = np.zeros(self.nfile + 1, dtype=np.uint64)
         self.total_slots = hg_batch_slots(self.h, self.slot_off.ctypes.data)
 
@@ -274,9 +304,13 @@ class Batch:
             hg_batch_destroy(self.h)
             self.h = None
 
+    def _release(self):
+        self.close()
+
     def __del__(self):
         try:
-            self.close()
+            if _finalizer_may_call():
+                self.close()
         except Exception:
             pass
 
@@ -360,6 +394,7 @@ class Server:
         self.cfg = cfg
         self.ctx = ctx
         self.h = hg_server_create(ctx.h, cfg)
+        _children.add(self)
         self._keep: dict[int, object] = {}
 
     @staticmethod
@@ -436,9 +471,13 @@ class Server:
             self.h = None
             self._keep.clear()
 
+    def _release(self):
+        self.close()
+
     def __del__(self):
         try:
-            self.close()
+            if _finalizer_may_call():
+                self.close()
         except Exception:
             pass
 
@@ -452,6 +491,7 @@ class CdcStream:
         self.p = p or default_params()
         self.max_feed = max_feed
         self.h = hg_stream_open(ctx.h, algo, self.p, max_feed)
+        _children.add(self)
         self.cap = (max_feed + self.p.max_chunk + self.p.window) // self.p.min_chunk + 2
         dev = ctx.device
         self._ends = torch.empty(self.cap, dtype=torch.int64, device=dev)
@@ -476,10 +516,15 @@ class CdcStream:
         self.h = None
         return out
 
+    def _release(self):
+        if self.h:
+            hg_stream_destroy(self.h)
+            self.h = None
+
     def __del__(self):
         try:
-            if self.h:
-                hg_stream_destroy(self.h)
+            if _finalizer_may_call():
+                self._release()
         except Exception:
             pass
 
@@ -490,6 +535,7 @@ class BlockMap:
     def __init__(self, ctx: Context, algo: int = MD5, capacity: int = 1 << 20):
         self.ctx, self.algo = ctx, algo
         self.h = hg_blockmap_create(ctx.h, algo, capacity)
+        _children.add(self)
 
     def insert(self, digests: torch.Tensor, count: torch.Tensor | None = None, stream=None):
         check(hg_blockmap_insert(self.h, _ptr(digests), digests.shape[0] if digests.dim() else 0,
@@ -521,8 +567,12 @@ class BlockMap:
             hg_blockmap_destroy(self.h)
             self.h = None
 
+    def _release(self):
+        self.close()
+
     def __del__(self):
         try:
-            self.close()
+            if _finalizer_may_call():
+                self.close()
         except Exception:
             pass
