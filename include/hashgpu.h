@@ -122,7 +122,10 @@ int hg_host_digest(int algo, const uint8_t *msg, uint64_t n, uint8_t *out);
  * time, after which calls on such inputs never synchronise.
  */
 int hg_init(hg_ctx **out, int device, size_t device_budget_bytes);
-/* Free the context and all its scratch (synchronises its device first). */
+/* Free the context and all its scratch (synchronises its device first).
+ * Destroy the objects made on a context (servers, batches, streams, block
+ * maps) before the context, and all of them before the process exits and the
+ * CUDA runtime is torn down; the Python binding does this in an exit handler. */
 int hg_destroy(hg_ctx *ctx);
 /* Pre-allocate scratch for chunking inputs of up to max_bytes bytes (may
  * synchronise the device once, see hg_init). HG_ENOMEM over the budget. */
