@@ -236,6 +236,26 @@ def test_cdc_hash_from_host(hg, n):
     assert torch.equal(dev.cpu(), host)
 
 
+@pytest.mark.parametrize("hoff,doff", [(3, 5), (1, 0), (0, 7)])
+def test_cdc_hash_from_host_unaligned(hg, hoff, doff):
+    """hg_cdc_hash_h2d with the host bytes and the device buffer at odd offsets (the device
+    side then takes the byte-load window path throughout)."""
+    n = (9 << 20) + 333
+    data = G.uniform_bytes(n, seed=n + hoff)
+    hbuf = torch.empty(n + 16, dtype=torch.uint8).pin_memory()
+    hbuf[hoff:hoff + n] = torch.from_numpy(data)
+    host = hbuf[hoff:hoff + n]
+    dbuf = torch.empty(n + 16, dtype=torch.uint8, device="cuda")
+    dev = dbuf[doff:doff + n]
+    ends, cnt, dg = hg.cdc_hash_from_host(host, dev, oracle.MD5)
+    hg.sync()
+    k = int(cnt.item())
+    want = oracle.cdc(data, nthreads=8)
+    assert np.array_equal(ends[:k].cpu().numpy().astype(np.uint64), want)
+    assert np.array_equal(dg[:k].cpu().numpy(), oracle.hash_chunks(oracle.MD5, data, want))
+    assert torch.equal(dev.cpu(), host)
+
+
 @pytest.mark.parametrize("pieces", [
     [1, 19, 20, 21, 5000, 65536, 65537, 1 << 20],
     [4096] * 300,
