@@ -276,16 +276,16 @@ def cpu_baseline(versions, budget_s: float = 12.0):
 
     # the other configurations, on samples sized from the rates above
     configs = {}
-    c1 = G.uniform_bytes(8 << 20, seed=1)
+    small = G.uniform_bytes(8 << 20, seed=1)
     for algo, name in ((oracle.MD5, "md5"), (oracle.SHA1, "sha1")):
-        configs[f"c1_8MiB_4KiB_{name}_with_root"] = {
-            "1_thread": _time_rate(lambda: oracle.hash_blocks(algo, c1, 4096, L=L), c1.size),
-            f"{nthreads}_threads": _time_rate(lambda: _oracle_blocks_n(oracle, L, algo, c1, 4096, nthreads),
-                                              c1.size)}
+        configs[f"blocks_8MiB_4KiB_{name}_with_root"] = {
+            "1_thread": _time_rate(lambda: oracle.hash_blocks(algo, small, 4096, L=L), small.size),
+            f"{nthreads}_threads": _time_rate(lambda: _oracle_blocks_n(oracle, L, algo, small, 4096, nthreads),
+                                              small.size)}
     u = G.uniform_bytes(64 << 20, seed=4)          # a 64 MiB sample drawn as the 1 GiB input is
     for algo, name in ((oracle.MD5, "md5"), (oracle.SHA1, "sha1")):
         for block, label in ((4096, "4KiB"), (1 << 20, "1MiB")):
-            configs[f"c3_uniform_{label}_{name}"] = {
+            configs[f"blocks_1GiB_uniform_{label}_{name}"] = {
                 "1_thread": _time_rate(lambda: oracle.hash_blocks(algo, u[:16 << 20], block, L=L), 16 << 20),
                 f"{nthreads}_threads": _time_rate(
                     lambda: _oracle_blocks_n(oracle, L, algo, u, block, nthreads), u.size)}
@@ -300,7 +300,7 @@ def cpu_baseline(versions, budget_s: float = 12.0):
         def cdc_one(d=data[:n1c]):
             e = oracle.cdc(d, nthreads=1, L=L)
             oracle.hash_chunks(oracle.MD5, d, e, L=L)
-        configs[f"c3_{dist}_cdc_md5"] = {"1_thread": _time_rate(cdc_one, n1c),
+        configs[f"cdc_1GiB_{dist}_md5"] = {"1_thread": _time_rate(cdc_one, n1c),
                                          f"{nthreads}_threads": _time_rate(cdc_all, data.size)}
     return {"value": total / dt / 1e9, "unit": UNIT, "cores": nthreads, "kind": "oracle",
             "single_thread": single, "cpu": cpu_info(), "configs": configs,
@@ -896,14 +896,14 @@ def configs_leg(hgb, ctx, dev, flush):
         return statistics.median(a.elapsed_time(b) for a, b in ts) / 1e3
 
     res = {}
-    c1 = torch.from_numpy(G.uniform_bytes(8 << 20, seed=1)).to(dev)
+    small = torch.from_numpy(G.uniform_bytes(8 << 20, seed=1)).to(dev)
     for algo, name in ((hgb.MD5, "md5"), (hgb.SHA1, "sha1")):
         dl = 16 if algo == hgb.MD5 else 20
         out = torch.empty((2048, dl), dtype=torch.uint8, device=dev)
         rt = torch.empty(dl, dtype=torch.uint8, device=dev)
-        t = med(lambda: ctx.hash_blocks(c1, 4096, algo, root=True, out=out, root_out=rt))
-        res[f"c1_8MiB_4KiB_{name}_with_root"] = {"ms": t * 1e3, "GBps": (8 << 20) / t / 1e9}
-    del c1
+        t = med(lambda: ctx.hash_blocks(small, 4096, algo, root=True, out=out, root_out=rt))
+        res[f"blocks_8MiB_4KiB_{name}_with_root"] = {"ms": t * 1e3, "GBps": (8 << 20) / t / 1e9}
+    del small
     n = 1 << 30
     d = torch.empty(n, dtype=torch.uint8, device=dev)
     cap = n // 2048 + 2
@@ -926,7 +926,7 @@ def configs_leg(hgb, ctx, dev, flush):
             h_dg.copy_(outs[2], non_blocking=True)
         t_e = med(e2e, reps=5)
         ctx.sync()
-        res[f"c3_1GiB_{dist}_cdc_md5"] = {"kernel_GBps": n / t_k / 1e9, "kernel_ms": t_k * 1e3,
+        res[f"cdc_1GiB_{dist}_md5"] = {"kernel_GBps": n / t_k / 1e9, "kernel_ms": t_k * 1e3,
                                            "e2e_GBps": n / t_e / 1e9, "e2e_ms": t_e * 1e3,
                                            "chunks": int(outs[1].item())}
         if dist == "uniform":
@@ -953,11 +953,11 @@ def configs_leg(hgb, ctx, dev, flush):
                     for st in streams:
                         s.wait_stream(st)
                 t_b = med(blocks_e2e, reps=5)
-                res[f"c3_1GiB_uniform_4KiB_{name}_e2e"] = {"GBps": n / t_b / 1e9, "ms": t_b * 1e3}
+                res[f"blocks_1GiB_uniform_4KiB_{name}_e2e"] = {"GBps": n / t_b / 1e9, "ms": t_b * 1e3}
         del host
     ctx.sync()
-    res["note"] = ("c1: one hg_hash_blocks call with the root (latency-bound: 2048 chains + one "
-                   "serial root); c3: hg_cdc_hash on device input vs hg_cdc_hash_h2d from pinned "
+    res["note"] = ("blocks_8MiB: one hg_hash_blocks call with the root (latency-bound: 2048 chains "
+                   "+ one serial root); cdc_1GiB: hg_cdc_hash on device input vs hg_cdc_hash_h2d from pinned "
                    "host memory (+ D2H of ends and digests); fixed-block e2e: 64 MiB pieces copied and "
                    "hashed on two streams, digests copied back (root not included)")
     return res
