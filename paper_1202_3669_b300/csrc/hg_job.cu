@@ -152,6 +152,14 @@ __global__ void __launch_bounds__(kWinThreads) k_job_window(JobDev j, uint32_t w
 // whichever file owns the tile; spans past the file's end write zero words.
 // Counts are added to the tile's count (zeroed before the launch). Selected by
 // the tuning's window_ctas_per_sm = 0.
+//
+// Files of a batch start at any byte. An interior span whose bytes do not
+// start on a 16-byte boundary is still staged by one bulk copy: the copy takes
+// the 16-byte granules that cover the span (its extra bytes lie in granules
+// that hold span bytes, so in the same mapped memory) into a second buffer,
+// and the warp shifts the words into place (9 funnel shifts a lane). The 4096-
+// file batch stored back to back took 43.79 ms with such spans staged by byte
+// loads, 42.24 ms with every file moved to a 16-byte aligned slot.
 template <int W>
 __global__ void __launch_bounds__(32, 32) k_job_window_span(JobDev j, uint32_t wrt, uint32_t mask,
                                                             uint32_t magic,
@@ -160,7 +168,9 @@ __global__ void __launch_bounds__(32, 32) k_job_window_span(JobDev j, uint32_t w
                                                             uint32_t one) {
     const uint32_t wlen = W ? (uint32_t)W : wrt;
     constexpr int kSub = (int)(kWinTile / kWinSpan);
-    __shared__ __align__(128) uint8_t sbuf[kHalo + kWinSpan + 16];
+    constexpr int kSpanBytes = kHalo + kWinSpan;              // a multiple of 16
+    __shared__ __align__(128) uint8_t sbuf[kSpanBytes + 16];
+    __shared__ __align__(128) uint8_t sraw[kSpanBytes + 16];  // granules of an unaligned span
     __shared__ __align__(8) uint64_t mbar;
     const int t = threadIdx.x;
     const uint32_t tile = blockIdx.x / kSub, sub = blockIdx.x % kSub;
@@ -169,19 +179,31 @@ __global__ void __launch_bounds__(32, 32) k_job_window_span(JobDev j, uint32_t w
     const uint64_t lo = r.lo + (uint64_t)sub * kWinSpan;
     uint32_t bits = 0;
     if (lo < r.len) {
-        const bool fast = ((reinterpret_cast<uintptr_t>(r.ptr) & 15) == 0) && lo >= (uint64_t)kHalo &&
-                          lo + kWinSpan <= r.len;
-        if (t < 4) reinterpret_cast<uint32_t *>(sbuf + kHalo + kWinSpan)[t] = 0;
+        const bool fast = lo >= (uint64_t)kHalo && lo + kWinSpan <= r.len;
+        if (t < 4) reinterpret_cast<uint32_t *>(sbuf + kSpanBytes)[t] = 0;
         bool timed_out = false;
         if (fast) {
+            const uint8_t *src = r.ptr + lo - kHalo;
+            const uint32_t a = (uint32_t)(reinterpret_cast<uintptr_t>(src) & 15);
             const uint32_t mb = smem_u32(&mbar);
             if (t == 0) mbar_init(mb);
             __syncwarp();
-            if (t == 0) bulk_load(smem_u32(sbuf), r.ptr + lo - kHalo, (uint32_t)(kHalo + kWinSpan), mb);
+            if (t == 0) {
+                if (a == 0) bulk_load(smem_u32(sbuf), src, (uint32_t)kSpanBytes, mb);
+                else bulk_load(smem_u32(sraw), src - a, (uint32_t)(kSpanBytes + 16), mb);
+            }
             timed_out = !mbar_wait(mb, 0);
             if (timed_out) {
                 atomicCAS(err, 0, (int)HG_ETIMEDOUT);
                 mbar_wait(mb, 0);
+            }
+            if (a != 0 && !timed_out) {
+                // span word i = bytes a + 4i .. a + 4i + 3 of the granules
+                const uint32_t *rw = reinterpret_cast<const uint32_t *>(sraw);
+                uint32_t *sw = reinterpret_cast<uint32_t *>(sbuf);
+                const uint32_t q = a >> 2, r8 = (a & 3) * 8;
+                for (int i = t; i < kSpanBytes / 4; i += 32)
+                    sw[i] = __funnelshift_r(rw[i + q], rw[i + q + 1], r8);
             }
         } else {
             for (int i = t; i < kHalo + kWinSpan; i += 32) {
