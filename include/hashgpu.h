@@ -369,7 +369,9 @@ int hg_batch_sync(hg_batch *batch, void *stream);
 int hg_batch_get_tuning(const hg_batch *batch, hg_batch_tuning *tuning);
 int hg_batch_set_tuning(hg_batch *batch, const hg_batch_tuning *tuning);
 /* Time a small set of tunings on this batch (synchronous: runs the batch about
- * 63 times) and keep the fastest; it is also written to *best if not NULL. */
+ * 100 times; each candidate keeps the fastest of three timed runs, the window
+ * forms are timed twice) and keep the fastest; it is also written to *best if
+ * not NULL. */
 int hg_batch_autotune(hg_batch *batch, int algo, const uint8_t *d_data, uint64_t *d_ends,
                       uint64_t *d_counts, uint8_t *d_digests, void *stream, hg_batch_tuning *best);
 /* hg_batch_autotune through a cache file (JSON Lines, one
