@@ -61,6 +61,30 @@ def test_server_default_config():
     assert (cfg.max_wave_requests, cfg.max_inflight_waves, cfg.cdc.window) == (4096, 3, 20)
 
 
+def test_exit_handler_closes_children_before_contexts():
+    """The binding's exit handler releases servers, streams, block maps and batches
+    before the contexts they were made on (host logic, with stand-in objects)."""
+    import paper_1202_3669_b300 as hgb
+    order = []
+
+    class Stub:
+        def __init__(self, name):
+            self.name = name
+
+        def _release(self):
+            order.append(self.name)
+
+    ctx, child = Stub("context"), Stub("batch")
+    hgb._contexts.add(ctx)
+    hgb._children.add(child)
+    try:
+        hgb._close_all()
+    finally:
+        hgb._contexts.discard(ctx)
+        hgb._children.discard(child)
+    assert order.index("batch") < order.index("context")
+
+
 def test_init_without_gpu_fails_cleanly():
     import torch
     if torch.cuda.is_available():
