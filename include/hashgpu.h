@@ -436,7 +436,8 @@ typedef struct {
     uint64_t wave_target_bytes;   /* a wave takes no further request once that would
                                      bring its input past this many bytes; a single
                                      larger request (up to max_wave_bytes) still forms
-                                     a wave of its own. 0: max_wave_bytes (256 MiB) */
+                                     a wave of its own; 0 means max_wave_bytes
+                                     (default 256 MiB) */
 } hg_server_config;
 
 typedef struct {
